@@ -1,0 +1,160 @@
+"""Seeded synthetic workloads of the IMEX finite-difference lattice Boltzmann path.
+
+This module holds problem definitions and seeded random draws only: grid sizes,
+domains, gas parameters, time steps and initial Riemann states.  It contains
+none of the method's arithmetic, so both the CUDA path and the CPU oracle used
+by the tests may take their inputs from it.
+
+Workloads (all inputs synthetic; the paper uses no dataset):
+
+* ``sod_1d``: two-state shock tube on [-0.5, 0.5], membrane at x = 0,
+  left (rho, u, P) = (1, 0, 1), right (0.125, 0, 0.1) (Sec. V).
+* ``quadrant_2d``: four-quadrant Riemann problem on [0, 1]^2 split at
+  (0.5, 0.5); each quadrant's (rho, u, v, P) drawn uniformly from a seed,
+  rho in [0.1, 1.5], u, v in [-1.2, 1.2], P in [0.03, 1.5].
+* ``lax_liu_2d``: the paper's configurations 11 and 12 of the 2-D Riemann
+  problem (Sec. V).
+* ``batched_1d``: independent two-state problems of uneven length and gamma.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    d: int
+    nx: int
+    ny: int
+    x0: float
+    x1: float
+    y0: float
+    y1: float
+    Qphi: int
+    Qchi: int
+    gamma: float
+    tau: float
+    dt: float
+    t_end: float
+    states: tuple          # 1-D: ((rho,u,P) left, right); 2-D: 4 x (rho,u,v,P), quadrants 1..4
+    xsplit: float
+    ysplit: float
+    bc: int = 0            # 0 outlet (zero-gradient), 1 periodic
+
+    @property
+    def nsteps(self) -> int:
+        return int(round(self.t_end / self.dt))
+
+    @property
+    def ncell(self) -> int:
+        return self.nx * (self.ny if self.d == 2 else 1)
+
+    @property
+    def npop(self) -> int:
+        return self.Qphi ** self.d + self.Qchi ** self.d
+
+    def states_array(self) -> np.ndarray:
+        return np.asarray(self.states, dtype=np.float64)
+
+    def replace(self, **kw) -> "Workload":
+        return dataclasses.replace(self, **kw)
+
+
+SOD_LEFT = (1.0, 0.0, 1.0)
+SOD_RIGHT = (0.125, 0.0, 0.1)
+
+
+def sod_1d(nx: int = 400, Q: int = 8, Qchi: int | None = None, gamma: float = 1.4,
+           tau: float = 1e-6, dt: float = 5e-5, t_end: float = 0.1) -> Workload:
+    """Shock tube: Nx = 400, Q = 8, gamma = 7/5, tau = 1e-6, dt = 5e-5, t = 0.1."""
+    return Workload("sod_1d", 1, nx, 1, -0.5, 0.5, 0.0, 1.0, Q, Q if Qchi is None else Qchi,
+                    gamma, tau, dt, t_end, (SOD_LEFT, SOD_RIGHT), 0.0, 0.0)
+
+
+def quadrant_states(seed: int) -> tuple:
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(4):
+        rho = rng.uniform(0.1, 1.5)
+        u = rng.uniform(-1.2, 1.2)
+        v = rng.uniform(-1.2, 1.2)
+        P = rng.uniform(0.03, 1.5)
+        out.append((float(rho), float(u), float(v), float(P)))
+    return tuple(out)
+
+
+def quadrant_2d(seed: int = 0, n: int = 512, Q: int = 8, gamma: float = 1.4, tau: float = 1e-6,
+                dt: float = 2.5e-5, t_end: float = 0.25) -> Workload:
+    """Four-quadrant Riemann problem: 512 x 512 on [0,1]^2, 8x8 velocities."""
+    return Workload(f"quadrant_2d_s{seed}", 2, n, n, 0.0, 1.0, 0.0, 1.0, Q, Q, gamma, tau, dt,
+                    t_end, quadrant_states(seed), 0.5, 0.5)
+
+
+# Sec. V: configurations 11 and 12 of the 2-D Riemann problem, quadrants
+# 1 (top right), 2 (top left), 3 (bottom left), 4 (bottom right): (rho, ux, uy, P).
+C11_STATES = ((1.0, 0.1, 0.0, 1.0), (0.5313, 0.8276, 0.0, 0.4), (0.8, 0.1, 0.0, 0.4),
+              (0.5313, 0.1, 0.7276, 0.4))
+C12_STATES = ((0.5313, 0.0, 0.0, 0.4), (1.0, 0.7276, 0.0, 1.0), (0.8, 0.0, 0.0, 1.0),
+              (1.0, 0.0, 0.7276, 1.0))
+
+
+def lax_liu_2d(config: int = 11, n: int = 400, Qphi: int = 5, Qchi: int = 3, tau: float = 1e-5,
+               dt: float = 5e-4) -> Workload:
+    """Sec. V: C11 to t = 0.3, C12 to t = 0.25 on [-0.5, 0.5]^2 split at the origin."""
+    states = C11_STATES if config == 11 else C12_STATES
+    t_end = 0.3 if config == 11 else 0.25
+    return Workload(f"lax_liu_c{config}", 2, n, n, -0.5, 0.5, -0.5, 0.5, Qphi, Qchi, 1.4, tau, dt,
+                    t_end, states, 0.0, 0.0)
+
+
+def batched_problems(seed: int = 0, nprob: int = 512, nx_lo: int = 256, nx_hi: int = 4096):
+    """Independent two-state problems: Nx ~ U[256, 4096], gamma ~ U[1.1, 5/3],
+    rho ~ U[0.1, 1], u ~ U[-0.5, 0.5], P ~ U[0.1, 1] on each side."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for _ in range(nprob):
+        nx = int(rng.integers(nx_lo, nx_hi + 1))
+        gamma = float(rng.uniform(1.1, 5.0 / 3.0))
+        left = (float(rng.uniform(0.1, 1.0)), float(rng.uniform(-0.5, 0.5)),
+                float(rng.uniform(0.1, 1.0)))
+        right = (float(rng.uniform(0.1, 1.0)), float(rng.uniform(-0.5, 0.5)),
+                 float(rng.uniform(0.1, 1.0)))
+        probs.append({"nx": nx, "gamma": gamma, "states": (left, right)})
+    return probs
+
+
+def smooth_fields_1d(nx: int, seed: int = 0, amp: float = 0.1, periodic: bool = True):
+    """Smooth periodic (rho, u, T) built from a few low Fourier modes."""
+    rng = np.random.default_rng(seed)
+    x = (np.arange(nx) + 0.5) / nx
+    def field(base, a):
+        f = np.full(nx, base)
+        for m in range(1, 4):
+            f = f + a * rng.uniform(-1, 1) / m * np.cos(2 * math.pi * m * x + rng.uniform(0, 2 * math.pi))
+        return f
+    return field(1.0, amp), field(0.0, amp), field(1.0, amp)
+
+
+def smooth_fields_2d(n: int, seed: int = 0, amp: float = 0.1):
+    rng = np.random.default_rng(seed)
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x, indexing="xy")  # shape (ny, nx)
+    def field(base, a):
+        f = np.full((n, n), base)
+        for mx in range(0, 3):
+            for my in range(0, 3):
+                if mx == my == 0:
+                    continue
+                f = f + a * rng.uniform(-1, 1) / (mx + my) * np.cos(
+                    2 * math.pi * (mx * X + my * Y) + rng.uniform(0, 2 * math.pi))
+        return f
+    return field(1.0, amp), field(0.0, amp), field(0.0, amp), field(1.0, amp)
+
+
+def random_populations(shape, seed: int = 0, lo: float = 0.5, hi: float = 1.5) -> np.ndarray:
+    """Uniform random population values (for element-wise kernel checks)."""
+    return np.random.default_rng(seed).uniform(lo, hi, size=shape)
