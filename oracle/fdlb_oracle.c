@@ -393,8 +393,10 @@ void orc_advect_line(const double* F, int S, long stride, double p, double ds, i
   }
   for (int g = 0; g < 5; ++g) {
     if (bc == 1) {
-      ext[g] = ext[S + g];          /* cell S-5+g */
-      ext[S + 5 + g] = ext[5 + g];  /* cell g */
+      /* periodic image of 0-based line position j is position j mod S */
+      const int left = ((g - 5) % S + S) % S, right = (S + g) % S;
+      ext[g] = ext[5 + left];
+      ext[S + 5 + g] = ext[5 + right];
     } else {
       ext[g] = ext[5];
       ext[S + 5 + g] = ext[S + 4];

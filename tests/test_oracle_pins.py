@@ -491,3 +491,18 @@ def test_time_order_three(oracle):
     e2 = np.abs(sols[2] - sols[32]).max()
     e4 = np.abs(sols[4] - sols[32]).max()
     assert 6.5 < e1 / e2 < 10 and 6.5 < e2 / e4 < 10, (e1, e2, e4)
+
+
+@pytest.mark.parametrize("S", [1, 2, 3, 4, 5, 7])
+def test_periodic_ghosts_short_lines(oracle, S):
+    """Periodic lines shorter than the 5-node halo: the advection of a line
+    equals that of the same data repeated several times (the images of a
+    periodic line are its cells taken modulo S)."""
+    rng = np.random.default_rng(S)
+    F = rng.uniform(0.5, 1.5, size=S)
+    rep = 12
+    for p in (1.3, -0.9):
+        a = oracle.advect_line(F, p, 0.1, bc=1)
+        b = oracle.advect_line(np.tile(F, rep), p, 0.1, bc=1)
+        np.testing.assert_allclose(a, b[:S], rtol=0, atol=1e-14)
+        np.testing.assert_allclose(a, b[S * (rep // 2):S * (rep // 2 + 1)], rtol=0, atol=1e-14)
