@@ -1,0 +1,323 @@
+"""Benchmark of the IMEX finite-difference lattice Boltzmann hot path on GB300.
+
+Workload: the 2-D four-quadrant Riemann problem, 512 x 512 cells, 8x8
+Gauss-Hermite velocities for phi and for chi (128 populations per cell),
+gamma = 7/5, tau = 1e-6, dt = 2.5e-5, binary64, outlet boundaries; the
+quadrant states are the seeded draw ``workloads.quadrant_2d(BENCH_SEED)``.
+A step is one full IMEX-SSP3(4,3,3) step: the three fused stage kernels.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs an independent
+replica of the problem on its own GPU (the single-grid path has no data-path
+collective); value is the sum over ranks of population updates divided by
+the slowest rank's time.
+
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores: each step is one oracle step on a bounded sample of the workload (the
+first 64 rows of the 512 x 512 grid, 8x8 velocities), scaled to the same
+unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-velocity updates/s per IMEX step and % HBM peak; adjoint/fwd cost; mixed vs FP64"
+UNIT = "cell-velocity updates/s"
+
+# Algorithmic binary64 flops per population and launch of each fused stage
+# kernel (FMA = 2): two MP-9 interface values per population (x and y), each
+# 17 (9-point F^L) + 2 (differences) + 2 (F^MP) + 3 (limiter test) = 24; the
+# flux difference 5; the stage's explicit part, moments and relaxation
+# (stage 3: 12 + 4 + 8; stage 4: 4 + 4 + 6; final: 2 + 4 + 4).  The limited
+# MP branch, divisions and per-cell equilibrium factors are not counted.
+FLOPS_PER_POP = {"stage3": 48 + 5 + 24, "stage4": 48 + 5 + 14, "final": 48 + 5 + 10}
+# Algorithmic HBM bytes per population and launch (binary64): arrays read and
+# written once each by the kernel (stage 3: F2, F, D -> F3, A4, Af; stage 4:
+# F3, A4, Af -> A4, Af; final: A4, Af -> F, D, F2).
+BYTES_PER_POP = {"stage3": 6 * 8, "stage4": 5 * 8, "final": 5 * 8}
+# binary64 peak: 152 SMs x 2 DFMA lanes/clk/SM (the 1.25 TFLOP/s nominal
+# figure of GB300 at 2070 MHz) x 2 flops x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[2:]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist_setup():
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline_sample(steps: int = 1, rows: int = 64):
+    """Oracle timing on the first `rows` rows of the workload (FP64, host)."""
+    from oracle import oracle as O
+    from paper_1909_08390_gb300 import workloads as W
+    wl = W.quadrant_2d(W.BENCH_SEED)
+    y1 = rows / wl.ny
+    pr = O.Problem(d=2, nx=wl.nx, ny=rows, x0=wl.x0, x1=wl.x1, y0=0.0, y1=y1, Qphi=wl.Qphi,
+                   Qchi=wl.Qchi, gamma=wl.gamma, tau=wl.tau, dt=wl.dt)
+    F0 = O.init_states(pr, wl.states, wl.xsplit, 0.5 * y1)
+    t0 = time.perf_counter()
+    O.step(pr, F0, steps)
+    dt = time.perf_counter() - t0
+    units = pr.npop * wl.nx * rows * steps
+    return units / dt, dt, f"{steps} oracle step(s) on {wl.nx}x{rows} cells x {pr.npop} populations"
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the FP64 CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_1909_08390_gb300 import workloads as W
+    O.build()
+    wl = W.quadrant_2d(W.BENCH_SEED)
+    rows = 64
+    y1 = rows / wl.ny
+    pr = O.Problem(d=2, nx=wl.nx, ny=rows, x0=wl.x0, x1=wl.x1, y0=0.0, y1=y1, Qphi=wl.Qphi,
+                   Qchi=wl.Qchi, gamma=wl.gamma, tau=wl.tau, dt=wl.dt)
+    F = O.init_states(pr, wl.states, wl.xsplit, 0.5 * y1)
+    F = O.step(pr, F, args.warmup)
+    t0 = time.perf_counter()
+    F = O.step(pr, F, args.steps)
+    el = time.perf_counter() - t0
+    units = pr.npop * wl.nx * rows * args.steps
+    value = units / el
+    sample = f"{args.steps} oracle steps on {wl.nx}x{rows} cells (first 64 rows) x {pr.npop} populations"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"quadrant_2d_s{W.BENCH_SEED} 512x512, 8x8 velocities, oracle sample",
+                   "sample_rows": rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_1909_08390_gb300 import build as B, fdlb, workloads as W
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        B.build()
+    _barrier(world)
+    fdlb.load()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    wl = W.quadrant_2d(W.BENCH_SEED)
+    s = fdlb.Solver.from_workload(wl, stream=stream)
+    s.init_riemann(wl.states, wl.xsplit, wl.ysplit)
+    P, N = s.P, s.N
+    units_per_step = P * N
+    launches_per_step = fdlb.fdlb_launches_per_step(s.ctx)
+
+    # warm-up
+    fdlb.fdlb_step(s.ctx, args.warmup)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, per-kernel CUDA events recorded inside the library
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        _barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        stage_ms = fdlb.fdlb_step_timed(s.ctx, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        _barrier(world)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    elapsed_ms = _max_over_ranks(world, elapsed_ms)
+    value = world * units_per_step * args.steps / (elapsed_ms * 1e-3)
+
+    # roofline of the dominant stage kernel
+    names = ["stage3", "stage4", "final"]
+    top = max(range(3), key=lambda i: stage_ms[i])
+    per_launch_ms = stage_ms[top] / args.steps
+    flops = FLOPS_PER_POP[names[top]] * units_per_step
+    achieved_tflops = flops / (per_launch_ms * 1e-3) / 1e12
+    hbm_bytes = BYTES_PER_POP[names[top]] * units_per_step
+    peaks = _load_peaks()
+    roofline = {
+        "bound": "alu", "kernel": f"stage_kernel<2,8,8,{names[top]}>",
+        "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": achieved_tflops / FP64_PEAK_TFLOPS,
+        "peak_source": "binary64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+        "traffic": None,
+        "algorithmic_flops_per_launch": flops,
+        "avg_launch_ms": per_launch_ms,
+        "stage_ms_per_step": {n: v / args.steps for n, v in zip(names, stage_ms)},
+        "hbm_achieved_gbs": hbm_bytes / (per_launch_ms * 1e-3) / 1e9,
+        "hbm_peak_gbs": peaks.get("hbm_gbs"),
+    }
+
+    # end to end through the C ABI with host buffers: per step, upload the
+    # state from pinned host memory, advance one step, read the moments back.
+    host_state = torch.empty(s.shape, dtype=torch.float64, pin_memory=True)
+    fdlb.fdlb_get_state(s.ctx, host_state.numpy(), False)
+    sh = s.shape[1:]
+    mom = [torch.empty(sh, dtype=torch.float64, pin_memory=True) for _ in range(4)]
+    e2e_steps = max(1, min(args.steps, 10))
+    torch.cuda.synchronize()
+    _barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fdlb.fdlb_set_state(s.ctx, host_state.numpy(), False)
+        fdlb.fdlb_step(s.ctx, 1)
+        fdlb.fdlb_moments(s.ctx, mom[0].numpy(), mom[1].numpy(), mom[2].numpy(), mom[3].numpy(),
+                          False)
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(world, time.perf_counter() - t0)
+    e2e = {"value": world * units_per_step * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(host_state.numel() * 8),
+           "d2h_bytes_per_step": int(4 * N * 8), "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, secs, sample = cpu_baseline_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": secs}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded four-quadrant Riemann states)",
+        "config": {"workload": f"quadrant_2d_s{W.BENCH_SEED} 512x512, 8x8 velocities (128 pops), "
+                               "gamma=1.4, tau=1e-6, dt=2.5e-5, FP64",
+                   "cells": int(N), "populations": int(P), "parallelism": f"replicas{world}",
+                   "l2": "working set 1.6 GB > 129 MB L2 (no flush needed)"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = _dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * fdlb.h -- C ABI of the GB300 (sm_103a) IMEX finite-difference lattice
+ * Boltzmann library (libfdlb.so).
+ *
+ * The library advances the two reduced distributions phi and chi of Kis &
+ * Ambrus, "Implicit-Explicit Finite-Difference Lattice Boltzmann Model with
+ * Varying Adiabatic Index":
+ *   - phi = int f d(eta) d(zeta), chi = int (eta^2 + zeta^2) f d(eta) d(zeta)
+ *     (Sec. II, Eq. galpha), so that D + K = 2/(gamma - 1) is free and gamma
+ *     is any adiabatic index with K + D - d >= 0;
+ *   - on the Gauss-Hermite product lattice of Qphi^d (phi) and Qchi^d (chi)
+ *     momenta, roots of He_Q, weights absorbed (Sec. II);
+ *   - with the Hermite-truncated equilibria of Eq. (gExpanded);
+ *   - advection by the MP-9 monotonicity-preserving flux of Sec. IV, one 1-D
+ *     sweep per axis, 5 ghost nodes per side (outlet: copies of the adjacent
+ *     fluid node);
+ *   - time stepping by the IMEX Runge-Kutta scheme of Eq. (IMEX) with the
+ *     IMEX-SSP3(4,3,3) tableaux of Table I, every implicit BGK stage solved in
+ *     closed form because collisions conserve n, u and T (Sec. III).
+ *
+ * Units: m = k_B = 1, momenta in units of the reference speed (Sec. II), so
+ * the lattice momenta are the raw Hermite roots and n = rho, T = P/rho.
+ *
+ * State layout (host and device copies alike): one contiguous array
+ *   F[P][ny][nx], x fastest (1-D: F[P][nx]), P = Qphi^d + Qchi^d;
+ *   populations 0 .. Qphi^d-1 are phi_k, k = ky*Qphi + kx (1-D: kx);
+ *   populations Qphi^d .. P-1 are chi_q, q = qy*Qchi + qx;
+ *   momenta in ascending order along each axis.
+ * Element type: double for FDLB_FP64 contexts, float for FDLB_MIXED contexts.
+ *
+ * Ownership: the context owns every device buffer it allocates (cudaMalloc in
+ * fdlb_create, freed by fdlb_destroy).  Callers own the arrays they pass in;
+ * on_device = 0 means a host pointer (pageable or pinned), on_device = 1 a
+ * device pointer of the context's device (e.g. a torch tensor's data_ptr()).
+ * All work is enqueued on the context's CUDA stream; calls that return data
+ * to host memory synchronise that stream before returning.
+ *
+ * Errors: every int-returning call returns FDLB_OK (0) or a negative code and
+ * never aborts the process; fdlb_last_error() gives a one-line reason.
+ * A context is not thread-safe: one caller thread at a time.
+ */
+#ifndef FDLB_H
+#define FDLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDLB_OK 0
+#define FDLB_EINVAL -1      /* bad argument: sizes, Q, gamma (K+D-d < 0), tau, dt, tableau */
+#define FDLB_ECFL -2        /* |p| dt / ds > 1 for some lattice momentum (Sec. IV) */
+#define FDLB_ENOMEM -3      /* device allocation failed */
+#define FDLB_ECUDA -4       /* a CUDA runtime call failed (message in fdlb_last_error) */
+#define FDLB_EUNSTABLE -5   /* a cell reached n <= 0, T <= 0 or a non-finite moment */
+#define FDLB_ETIMEOUT -6    /* reserved: a bounded device wait gave up */
+
+#define FDLB_FP64 0         /* populations stored and computed in binary64 */
+#define FDLB_MIXED 1        /* reserved: binary32 storage and advection, binary64 moments */
+
+#define FDLB_BC_OUTLET 0    /* ghosts copy the adjacent fluid node (Sec. IV) */
+#define FDLB_BC_PERIODIC 1  /* periodic images (conservation tests) */
+
+typedef struct fdlb_ctx fdlb_ctx; /* opaque, library-owned */
+
+/* Grid: d = 1 or 2 inhomogeneous axes, nx (and ny when d = 2) cells of the
+ * domain [x0, x1] (x [y0, y1]); cell centres x_s = x0 + (s - 1/2) dx,
+ * dx = (x1 - x0)/nx (Sec. IV).  bc is FDLB_BC_OUTLET or FDLB_BC_PERIODIC. */
+typedef struct {
+  int d;
+  int64_t nx, ny;
+  double x0, x1, y0, y1;
+  int bc;
+} fdlb_grid;
+
+/* An r-stage IMEX tableau, row-major r x r: At (explicit, strictly lower),
+ * A (implicit, lower), weights wt (explicit) and w (implicit).  The fused
+ * kernels take any r = 4 tableau in which stage 1 is never advected
+ * (At[i][0] = 0 for all i, wt[0] = 0) and stage 2 is not advected into
+ * (At[1][*] = 0), as in Table I; others are rejected with FDLB_EINVAL. */
+typedef struct {
+  int r;
+  double At[16], A[16], wt[4], w[4];
+} fdlb_tableau;
+
+/* Create a context and allocate its device buffers on the current device.
+ *   grid       : see fdlb_grid (nx, ny >= 1; x1 > x0; y1 > y0 when d = 2)
+ *   Qphi, Qchi : Gauss-Hermite orders per axis; supported pairs (8,8), (5,3),
+ *                (3,3) in 1-D and 2-D
+ *   gamma      : adiabatic index, D + K = 2/(gamma - 1), needs D + K >= d
+ *   tau, dt    : BGK relaxation time (> 0) and time step (> 0);
+ *                dt max|p| / dx <= 1 on every axis (Sec. IV CFL condition)
+ *   tableau    : NULL for IMEX-SSP3(4,3,3) of Table I
+ *   precision  : FDLB_FP64
+ *   cuda_stream: cudaStream_t to enqueue on (NULL: the legacy default stream)
+ *   out        : receives the context (NULL on failure)
+ * The populations start at zero; call fdlb_init_riemann or fdlb_set_state. */
+int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double tau, double dt,
+                const fdlb_tableau* tableau, int precision, void* cuda_stream, fdlb_ctx** out);
+
+/* Set F to the discrete equilibrium (Eq. gExpanded) of piecewise-constant
+ * Riemann data (Sec. V), n = rho, T = P/rho.
+ *   1-D: nq = 2, states = {rho, u, P} left of xsplit, then right (cells with
+ *        centre x >= xsplit take the right state);
+ *   2-D: nq = 4, states = {rho, ux, uy, P} for quadrants 1 (x >= xsplit,
+ *        y >= ysplit), 2 (x < xsplit, y >= ysplit), 3 (x < xsplit,
+ *        y < ysplit) and 4 (x >= xsplit, y < ysplit).
+ * states is a host array of nq*(d+2) doubles; rho > 0 and P > 0 required. */
+int fdlb_init_riemann(fdlb_ctx* ctx, const double* states, int nq, double xsplit, double ysplit);
+
+/* Advance nsteps >= 0 full IMEX steps (all r stages) on the context's stream.
+ * Returns FDLB_EUNSTABLE if any cell's moments became invalid during these
+ * steps (checked once, after the last step, from a device status word). */
+int fdlb_step(fdlb_ctx* ctx, int64_t nsteps);
+
+/* fdlb_step that also reports, in stage_ms[0..2], the device time summed over
+ * the nsteps steps of each fused kernel kind: stage 3, stage 4 and the final
+ * stage (which also forms the next step's stage 2), from CUDA events recorded
+ * on the context's stream between consecutive launches.  stage_ms is a host
+ * array of 3 doubles. */
+int fdlb_step_timed(fdlb_ctx* ctx, int64_t nsteps, double* stage_ms);
+
+/* Moments of the current state (Eq. Moments_discrete): n, ux, uy (2-D only,
+ * may be NULL in 1-D), T, each ncells = nx*ny doubles in [ny][nx] order.
+ * on_device selects host or device destination pointers. */
+int fdlb_moments(fdlb_ctx* ctx, double* n, double* ux, double* uy, double* T, int on_device);
+
+/* Copy the whole state F (layout above) out of / into the context.
+ * fdlb_state_bytes gives the size: P * ncells * element size. */
+size_t fdlb_state_bytes(const fdlb_ctx* ctx);
+int fdlb_get_state(fdlb_ctx* ctx, void* dst, int on_device);
+int fdlb_set_state(fdlb_ctx* ctx, const void* src, int on_device);
+
+/* Number of populations P and cells of the context (0 for NULL). */
+int fdlb_npop(const fdlb_ctx* ctx);
+int64_t fdlb_ncells(const fdlb_ctx* ctx);
+
+/* Replace the context's stream (cudaStream_t, NULL = legacy default). */
+int fdlb_set_stream(fdlb_ctx* ctx, void* cuda_stream);
+
+/* Number of kernel launches fdlb_step makes per step (for launch accounting). */
+int fdlb_launches_per_step(const fdlb_ctx* ctx);
+
+/* The Gauss-Hermite rule of order Q (1 <= Q <= 16) the library uses for
+ * weight exp(-p^2/2)/sqrt(2 pi): p[0..Q-1] the roots of He_Q in ascending
+ * order, w[0..Q-1] = Q!/He_{Q+1}(p_k)^2 (Sec. II).  Host arrays; no GPU
+ * needed.  Returns FDLB_EINVAL for Q out of range or NULL arrays. */
+int fdlb_lattice_nodes(int Q, double* p, double* w);
+
+/* Release the context and its device buffers (NULL is a no-op). */
+void fdlb_destroy(fdlb_ctx* ctx);
+
+/* One-line description of the last error on ctx (or of the last failed
+ * fdlb_create when ctx is NULL); never NULL. */
+const char* fdlb_last_error(const fdlb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDLB_H */

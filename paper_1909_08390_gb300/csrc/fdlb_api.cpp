@@ -1,0 +1,519 @@
+// fdlb_api.cpp -- host side of libfdlb.so: the C ABI declared in
+// include/fdlb.h, lattice construction, validation and stage coefficients.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fdlb.h"
+#include "fdlb_internal.h"
+
+using fdlb::DevParams;
+using fdlb::kMaxQ;
+
+struct fdlb_ctx {
+  DevParams dp{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int precision = FDLB_FP64;
+  fdlb_grid grid{};
+  double gamma = 0, tau = 0, dt = 0;
+  void* buf = nullptr;  // one allocation: 6 population arrays, 4 moment fields, status
+  double* mom = nullptr;  // device moments buffer (n, ux, uy, T) for host copies
+  size_t buf_bytes = 0;
+  unsigned* status_host = nullptr;  // pinned
+  bool prepared = false;
+  std::string err;
+};
+
+namespace {
+
+std::string g_create_error = "no error";
+
+int set_err(fdlb_ctx* c, int code, const char* fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_err(fdlb_ctx* c, cudaError_t e, const char* what) {
+  return set_err(c, FDLB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// He_n(x) (probabilists') and He_n'(x) = n He_{n-1}(x) by the recurrence
+// He_{k+1} = x He_k - k He_{k-1}.
+void hermite(int n, long double x, long double* h, long double* dh) {
+  long double hm1 = 0.0L, h0 = 1.0L;
+  for (int k = 0; k < n; ++k) {
+    long double hp = x * h0 - (long double)k * hm1;
+    hm1 = h0;
+    h0 = hp;
+  }
+  *h = h0;
+  *dh = (long double)n * hm1;
+}
+
+// Gauss-Hermite rule for the weight exp(-p^2/2)/sqrt(2 pi): the Q roots of
+// He_Q by simultaneous Newton (Ehrlich-Aberth) iteration from Chebyshev-spaced
+// starting points, then exact antisymmetry p_{Q-1-k} = -p_k, and weights
+// w_k = Q!/He_{Q+1}(p_k)^2 (Sec. II).
+bool gauss_hermite(int Q, double* p_out, double* w_out) {
+  if (Q < 1 || Q > kMaxQ) return false;
+  long double z[kMaxQ];
+  const long double R = sqrtl(4.0L * Q + 2.0L);
+  for (int i = 0; i < Q; ++i)
+    z[i] = -R * cosl(3.14159265358979323846L * (i + 0.5L) / Q) * 0.9L;
+  for (int it = 0; it < 500; ++it) {
+    long double maxstep = 0.0L;
+    for (int i = 0; i < Q; ++i) {
+      long double h, dh;
+      hermite(Q, z[i], &h, &dh);
+      if (h == 0.0L) continue;
+      const long double ratio = h / dh;
+      long double s = 0.0L;
+      for (int j = 0; j < Q; ++j)
+        if (j != i) s += 1.0L / (z[i] - z[j]);
+      const long double step = ratio / (1.0L - ratio * s);
+      z[i] -= step;
+      if (fabsl(step) > maxstep) maxstep = fabsl(step);
+    }
+    if (maxstep < 1e-30L) break;
+  }
+  // sort ascending (insertion sort) and enforce p(-x) symmetry
+  for (int i = 1; i < Q; ++i)
+    for (int j = i; j > 0 && z[j] < z[j - 1]; --j) {
+      long double t = z[j];
+      z[j] = z[j - 1];
+      z[j - 1] = t;
+    }
+  for (int i = 0; i < Q / 2; ++i) {
+    const long double a = 0.5L * (z[Q - 1 - i] - z[i]);
+    z[i] = -a;
+    z[Q - 1 - i] = a;
+  }
+  if (Q % 2 == 1) z[Q / 2] = 0.0L;
+  long double qf = 1.0L;
+  for (int k = 2; k <= Q; ++k) qf *= (long double)k;
+  for (int i = 0; i < Q; ++i) {
+    long double h, dh;
+    hermite(Q + 1, z[i], &h, &dh);
+    p_out[i] = (double)z[i];
+    w_out[i] = (double)(qf / (h * h));
+  }
+  // converged: the Newton correction at every root is below 1e-15 (1 + |p|)
+  for (int i = 0; i < Q; ++i) {
+    long double h, dh;
+    hermite(Q, z[i], &h, &dh);
+    if (!(fabsl(h / dh) <= 1e-15L * (1.0L + fabsl(z[i])))) return false;
+  }
+  return true;
+}
+
+// wH[l*kMaxQ + k] = w_k He_l(p_k) / l!
+void weighted_hermite_table(int Q, const double* p, const double* w, double* wH) {
+  for (int k = 0; k < Q; ++k) {
+    long double hm1 = 0.0L, h0 = 1.0L, fl = 1.0L;
+    for (int l = 0; l < Q; ++l) {
+      if (l > 0) fl *= (long double)l;
+      wH[l * kMaxQ + k] = (double)((long double)w[k] * h0 / fl);
+      long double hp = (long double)p[k] * h0 - (long double)l * hm1;
+      hm1 = h0;
+      h0 = hp;
+    }
+  }
+}
+
+void paper_tableau(fdlb_tableau* t) {
+  // Table I: IMEX-SSP3(4,3,3)
+  const double al = 0.24169426078821, be = 0.06042356519705, et = 0.12915286960590;
+  std::memset(t, 0, sizeof *t);
+  t->r = 4;
+  t->At[2 * 4 + 1] = 1.0;
+  t->At[3 * 4 + 1] = 0.25;
+  t->At[3 * 4 + 2] = 0.25;
+  t->A[0 * 4 + 0] = al;
+  t->A[1 * 4 + 0] = -al;
+  t->A[1 * 4 + 1] = al;
+  t->A[2 * 4 + 1] = 1.0 - al;
+  t->A[2 * 4 + 2] = al;
+  t->A[3 * 4 + 0] = be;
+  t->A[3 * 4 + 1] = et;
+  t->A[3 * 4 + 2] = 0.5 - be - et - al;
+  t->A[3 * 4 + 3] = al;
+  t->wt[1] = t->wt[2] = 1.0 / 6.0;
+  t->wt[3] = 2.0 / 3.0;
+  t->w[1] = t->w[2] = 1.0 / 6.0;
+  t->w[3] = 2.0 / 3.0;
+}
+
+// Reduce a supported tableau to the fused-stage coefficients (see
+// fdlb_internal.h for the algebra).
+bool stage_coefficients(const fdlb_tableau& t, double lam, fdlb::StageCoef* sc, const char** why) {
+  if (t.r != 4) { *why = "the fused kernels need r = 4 stages"; return false; }
+  auto At = [&](int i, int j) { return t.At[i * 4 + j]; };
+  auto A = [&](int i, int j) { return t.A[i * 4 + j]; };
+  for (int i = 0; i < 4; ++i) {
+    if (At(i, 0) != 0.0) { *why = "stage 1 must not be advected (At[i][0] = 0)"; return false; }
+    for (int j = i; j < 4; ++j)
+      if (At(i, j) != 0.0) { *why = "At must be strictly lower triangular"; return false; }
+    for (int j = i + 1; j < 4; ++j)
+      if (A(i, j) != 0.0) { *why = "A must be lower triangular"; return false; }
+  }
+  if (t.wt[0] != 0.0) { *why = "wt[0] must be 0"; return false; }
+  double e[4];
+  for (int i = 0; i < 4; ++i) {
+    const double den = 1.0 + A(i, i) * lam;
+    if (!(den > 0.0)) { *why = "1 + a_ii dt/tau must be positive"; return false; }
+    e[i] = lam / den;
+  }
+  // dF1 = e1 D; R2 = F - a21 dF1, dF2 = e2 (1 - a21 e1) D; F2 = F - a21 dF1 - a22 dF2
+  const double d1 = e[0];
+  const double d2 = e[1] * (1.0 - A(1, 0) * d1);
+  sc->c2 = 1.0 - A(1, 0) * d1 - A(1, 1) * d2;
+  sc->k3 = A(2, 0) * d1 + A(2, 1) * d2;
+  sc->k4 = A(3, 0) * d1 + A(3, 1) * d2;
+  sc->kf = t.w[0] * d1 + t.w[1] * d2;
+  sc->at32 = At(2, 1);
+  sc->at42 = At(3, 1);
+  sc->at43 = At(3, 2);
+  sc->wt2 = t.wt[1];
+  sc->wt3 = t.wt[2];
+  sc->wt4 = t.wt[3];
+  sc->a33e3 = A(2, 2) * e[2];
+  sc->a43e3 = A(3, 2) * e[2];
+  sc->w3e3 = t.w[2] * e[2];
+  sc->a44e4 = A(3, 3) * e[3];
+  sc->w4e4 = t.w[3] * e[3];
+  return true;
+}
+
+int ensure_prepared(fdlb_ctx* c) {
+  if (c->prepared) return FDLB_OK;
+  cudaError_t me = cudaMemsetAsync(c->dp.status, 0, sizeof(unsigned), c->stream);
+  if (me != cudaSuccess) return cuda_err(c, me, "status reset");
+  int e = fdlb::launch_stage(c->dp, fdlb::kPrep, c->stream);
+  if (e) return cuda_err(c, (cudaError_t)e, "prepare kernel launch");
+  c->prepared = true;
+  return FDLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double tau, double dt,
+                const fdlb_tableau* tableau, int precision, void* cuda_stream, fdlb_ctx** out) {
+  if (!out) return set_err(nullptr, FDLB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!grid) return set_err(nullptr, FDLB_EINVAL, "grid is NULL");
+  const fdlb_grid& g = *grid;
+  if (g.d != 1 && g.d != 2) return set_err(nullptr, FDLB_EINVAL, "d must be 1 or 2 (got %d)", g.d);
+  const int64_t ny = (g.d == 2) ? g.ny : 1;
+  if (g.nx < 1 || ny < 1 || g.nx > (1 << 30) || ny > (1 << 30))
+    return set_err(nullptr, FDLB_EINVAL, "bad cell counts nx=%lld ny=%lld", (long long)g.nx,
+                   (long long)g.ny);
+  if (!(g.x1 > g.x0) || (g.d == 2 && !(g.y1 > g.y0)))
+    return set_err(nullptr, FDLB_EINVAL, "empty domain");
+  if (g.bc != FDLB_BC_OUTLET && g.bc != FDLB_BC_PERIODIC)
+    return set_err(nullptr, FDLB_EINVAL, "bc must be 0 (outlet) or 1 (periodic)");
+  if (precision != FDLB_FP64)
+    return set_err(nullptr, FDLB_EINVAL, "precision %d not available (FDLB_FP64 only)", precision);
+  if (!fdlb::supported_lattice(g.d, Qphi, Qchi))
+    return set_err(nullptr, FDLB_EINVAL, "lattice d=%d Qphi=%d Qchi=%d not compiled", g.d, Qphi,
+                   Qchi);
+  if (!(gamma > 1.0) || !std::isfinite(gamma))
+    return set_err(nullptr, FDLB_EINVAL, "gamma must be > 1");
+  const double DK = 2.0 / (gamma - 1.0);
+  if (DK - g.d < 0.0)
+    return set_err(nullptr, FDLB_EINVAL, "gamma=%g gives D+K-d=%g < 0", gamma, DK - g.d);
+  if (!(tau > 0.0) || !(dt > 0.0) || !std::isfinite(tau) || !std::isfinite(dt))
+    return set_err(nullptr, FDLB_EINVAL, "tau and dt must be positive");
+  const int64_t N = g.nx * ny;
+  if (N > ((int64_t)1 << 31) / 2) return set_err(nullptr, FDLB_EINVAL, "too many cells");
+
+  fdlb_tableau tab;
+  if (tableau) tab = *tableau;
+  else paper_tableau(&tab);
+
+  fdlb_ctx* c = new (std::nothrow) fdlb_ctx();
+  if (!c) return set_err(nullptr, FDLB_ENOMEM, "host allocation failed");
+  c->grid = g;
+  c->grid.ny = ny;
+  c->gamma = gamma;
+  c->tau = tau;
+  c->dt = dt;
+  c->precision = precision;
+  c->stream = (cudaStream_t)cuda_stream;
+  DevParams& p = c->dp;
+  p.d = g.d;
+  p.nx = (int)g.nx;
+  p.ny = (int)ny;
+  p.bc = g.bc;
+  p.Qp = Qphi;
+  p.Qc = Qchi;
+  p.nphi = g.d == 1 ? Qphi : Qphi * Qphi;
+  p.nchi = g.d == 1 ? Qchi : Qchi * Qchi;
+  p.P = p.nphi + p.nchi;
+  p.N = N;
+  p.DK = DK;
+  p.kchi = DK - g.d;
+  const double dx = (g.x1 - g.x0) / (double)g.nx;
+  const double dy = (g.d == 2) ? (g.y1 - g.y0) / (double)ny : 1.0;
+  p.dtdx = dt / dx;
+  p.dtdy = (g.d == 2) ? dt / dy : 0.0;
+  double wp[kMaxQ], wc[kMaxQ];
+  if (!gauss_hermite(Qphi, p.pp, wp) || !gauss_hermite(Qchi, p.pc, wc)) {
+    delete c;
+    return set_err(nullptr, FDLB_EINVAL, "Gauss-Hermite rule failed to converge");
+  }
+  weighted_hermite_table(Qphi, p.pp, wp, p.wHp);
+  weighted_hermite_table(Qchi, p.pc, wc, p.wHc);
+  // CFL condition |p| dt / ds <= 1 for all momenta (Sec. IV)
+  const double pmax = std::fmax(std::fabs(p.pp[Qphi - 1]), std::fabs(p.pc[Qchi - 1]));
+  const double cfl = pmax * std::fmax(p.dtdx, p.dtdy);
+  if (cfl > 1.0) {
+    delete c;
+    return set_err(nullptr, FDLB_ECFL, "CFL = %g > 1", cfl);
+  }
+  p.invDK = 1.0 / DK;
+  for (int pop = 0; pop < p.P; ++pop) {
+    double ax, ay;
+    if (pop < p.nphi) {
+      ax = p.pp[g.d == 1 ? pop : pop % Qphi];
+      ay = g.d == 1 ? 0.0 : p.pp[pop / Qphi];
+      p.p2[pop] = ax * ax + ay * ay;
+    } else {
+      const int q = pop - p.nphi;
+      ax = p.pc[g.d == 1 ? q : q % Qchi];
+      ay = g.d == 1 ? 0.0 : p.pc[q / Qchi];
+      p.p2[pop] = 0.0;
+    }
+    p.px[pop] = ax;
+    p.py[pop] = ay;
+    p.cx[pop] = p.dtdx * ax;
+    p.cy[pop] = p.dtdy * ay;
+  }
+  const char* why = nullptr;
+  if (!stage_coefficients(tab, dt / tau, &p.sc, &why)) {
+    delete c;
+    return set_err(nullptr, FDLB_EINVAL, "unsupported tableau: %s", why);
+  }
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_err(nullptr, e, "cudaGetDevice");
+  }
+  const size_t arr = (size_t)p.P * (size_t)N * sizeof(double);
+  const size_t mom_bytes = 4 * (size_t)N * sizeof(double);
+  c->buf_bytes = 6 * arr + mom_bytes + 256;
+  e = cudaMalloc(&c->buf, c->buf_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    const size_t want = c->buf_bytes;
+    delete c;
+    return set_err(nullptr, FDLB_ENOMEM, "cudaMalloc(%zu) failed: %s", want,
+                   cudaGetErrorString(e));
+  }
+  char* b = (char*)c->buf;
+  p.F = (double*)(b + 0 * arr);
+  p.F2 = (double*)(b + 1 * arr);
+  p.F3 = (double*)(b + 2 * arr);
+  p.A4 = (double*)(b + 3 * arr);
+  p.Af = (double*)(b + 4 * arr);
+  p.D = (double*)(b + 5 * arr);
+  c->mom = (double*)(b + 6 * arr);
+  p.status = (unsigned*)(b + 6 * arr + mom_bytes);
+  e = cudaMallocHost(&c->status_host, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->buf, 0, c->buf_bytes, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    int rc = cuda_err(nullptr, e, "context set-up");
+    fdlb_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return FDLB_OK;
+}
+
+int fdlb_init_riemann(fdlb_ctx* c, const double* states, int nq, double xsplit, double ysplit) {
+  if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
+  if (!states) return set_err(c, FDLB_EINVAL, "states is NULL");
+  const int d = c->dp.d;
+  if ((d == 1 && nq != 2) || (d == 2 && nq != 4))
+    return set_err(c, FDLB_EINVAL, "nq must be 2 in 1-D and 4 in 2-D");
+  const int w = d + 2;
+  for (int q = 0; q < nq; ++q) {
+    const double rho = states[q * w], P = states[q * w + w - 1];
+    for (int j = 0; j < w; ++j)
+      if (!std::isfinite(states[q * w + j])) return set_err(c, FDLB_EINVAL, "non-finite state");
+    if (!(rho > 0.0) || !(P > 0.0)) return set_err(c, FDLB_EINVAL, "rho and P must be > 0");
+  }
+  const fdlb_grid& g = c->grid;
+  const double dx = (g.x1 - g.x0) / (double)g.nx;
+  const double dy = (d == 2) ? (g.y1 - g.y0) / (double)g.ny : 0.0;
+  int e = fdlb::launch_init_riemann(c->dp, states, nq, xsplit, ysplit, g.x0, dx, g.y0, dy,
+                                    c->stream);
+  if (e) return cuda_err(c, (cudaError_t)e, "init kernel launch");
+  c->prepared = false;
+  return ensure_prepared(c);
+}
+
+int fdlb_step(fdlb_ctx* c, int64_t nsteps) {
+  if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return set_err(c, FDLB_EINVAL, "nsteps < 0");
+  int rc = ensure_prepared(c);
+  if (rc) return rc;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    for (int st : {fdlb::kStage3, fdlb::kStage4, fdlb::kFinal}) {
+      int e = fdlb::launch_stage(c->dp, st, c->stream);
+      if (e) return cuda_err(c, (cudaError_t)e, "stage kernel launch");
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(c->status_host, c->dp.status, sizeof(unsigned),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "fdlb_step");
+  if (*c->status_host & 1u)
+    return set_err(c, FDLB_EUNSTABLE, "a cell reached n <= 0, T <= 0 or a non-finite moment");
+  return FDLB_OK;
+}
+
+int fdlb_step_timed(fdlb_ctx* c, int64_t nsteps, double* stage_ms) {
+  if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
+  if (nsteps < 0 || !stage_ms) return set_err(c, FDLB_EINVAL, "bad nsteps or stage_ms");
+  for (int i = 0; i < 3; ++i) stage_ms[i] = 0.0;
+  int rc = ensure_prepared(c);
+  if (rc) return rc;
+  const int kinds[3] = {fdlb::kStage3, fdlb::kStage4, fdlb::kFinal};
+  const size_t nev = (size_t)(3 * nsteps + 1);
+  std::vector<cudaEvent_t> ev(nev, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < nev && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
+  for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s) {
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+      int le = fdlb::launch_stage(c->dp, kinds[k], c->stream);
+      if (le) e = (cudaError_t)le;
+      if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + k + 1], c->stream);
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->status_host, c->dp.status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s)
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+      float ms = 0.0f;
+      e = cudaEventElapsedTime(&ms, ev[3 * s + k], ev[3 * s + k + 1]);
+      stage_ms[k] += ms;
+    }
+  for (size_t i = 0; i < nev; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess) return cuda_err(c, e, "fdlb_step_timed");
+  if (*c->status_host & 1u)
+    return set_err(c, FDLB_EUNSTABLE, "a cell reached n <= 0, T <= 0 or a non-finite moment");
+  return FDLB_OK;
+}
+
+int fdlb_moments(fdlb_ctx* c, double* n, double* ux, double* uy, double* T, int on_device) {
+  if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
+  if (!n || !ux || !T || (c->dp.d == 2 && !uy))
+    return set_err(c, FDLB_EINVAL, "NULL output pointer");
+  const int64_t N = c->dp.N;
+  if (on_device) {
+    int e = fdlb::launch_moments(c->dp, n, ux, c->dp.d == 2 ? uy : nullptr, T, c->stream);
+    if (e) return cuda_err(c, (cudaError_t)e, "moments kernel launch");
+    return FDLB_OK;
+  }
+  double* tmp = c->mom;
+  int le = fdlb::launch_moments(c->dp, tmp, tmp + N, c->dp.d == 2 ? tmp + 2 * N : nullptr,
+                                tmp + 3 * N, c->stream);
+  if (le) return cuda_err(c, (cudaError_t)le, "moments kernel launch");
+  double* dst[4] = {n, ux, c->dp.d == 2 ? uy : nullptr, T};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+    if (dst[i])
+      e = cudaMemcpyAsync(dst[i], tmp + i * N, N * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "fdlb_moments copy");
+  return FDLB_OK;
+}
+
+size_t fdlb_state_bytes(const fdlb_ctx* c) {
+  if (!c) return 0;
+  return (size_t)c->dp.P * (size_t)c->dp.N * sizeof(double);
+}
+
+int fdlb_get_state(fdlb_ctx* c, void* dst, int on_device) {
+  if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
+  if (!dst) return set_err(c, FDLB_EINVAL, "dst is NULL");
+  cudaError_t e = cudaMemcpyAsync(dst, c->dp.F, fdlb_state_bytes(c),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "fdlb_get_state");
+  return FDLB_OK;
+}
+
+int fdlb_set_state(fdlb_ctx* c, const void* src, int on_device) {
+  if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
+  if (!src) return set_err(c, FDLB_EINVAL, "src is NULL");
+  cudaError_t e = cudaMemcpyAsync(c->dp.F, src, fdlb_state_bytes(c),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "fdlb_set_state");
+  c->prepared = false;
+  int rc = ensure_prepared(c);
+  if (rc) return rc;
+  if (!on_device) {
+    // the source may be pageable memory the caller frees right after
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_err(c, e, "fdlb_set_state");
+  }
+  return FDLB_OK;
+}
+
+int fdlb_lattice_nodes(int Q, double* p, double* w) {
+  if (!p || !w || Q < 1 || Q > kMaxQ) return set_err(nullptr, FDLB_EINVAL, "bad Q or NULL arrays");
+  if (!gauss_hermite(Q, p, w)) return set_err(nullptr, FDLB_EINVAL, "Gauss-Hermite rule failed");
+  return FDLB_OK;
+}
+
+int fdlb_npop(const fdlb_ctx* c) { return c ? c->dp.P : 0; }
+
+int64_t fdlb_ncells(const fdlb_ctx* c) { return c ? c->dp.N : 0; }
+
+int fdlb_set_stream(fdlb_ctx* c, void* stream) {
+  if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
+  c->stream = (cudaStream_t)stream;
+  return FDLB_OK;
+}
+
+int fdlb_launches_per_step(const fdlb_ctx* c) { return c ? 3 : 0; }
+
+void fdlb_destroy(fdlb_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  if (c->buf) cudaFree(c->buf);
+  if (c->status_host) cudaFreeHost(c->status_host);
+  delete c;
+}
+
+const char* fdlb_last_error(const fdlb_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.empty() ? "no error" : c->err.c_str();
+}
+
+}  // extern "C"

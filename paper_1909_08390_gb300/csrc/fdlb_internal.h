@@ -1,0 +1,67 @@
+// fdlb_internal.h -- parameters shared by the host API (fdlb_api.cpp) and the
+// sm_103a kernels (fdlb_kernels.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace fdlb {
+
+constexpr int kMaxQ = 16;  // largest Gauss-Hermite order per axis
+constexpr int kMaxPop = 128;  // largest population count of a compiled lattice (2-D, Q = 8)
+
+// Coefficients of the fused IMEX stages.  With lam = dt/tau, e_i = lam/(1 +
+// a_ii lam) and D = F^n - F^n_eq, the stages of Eq. (IMEX) for a tableau whose
+// first stage is never advected reduce to (X_i = dt * L F^(i)):
+//   dF1 = e1 D,  dF2 = e2 D,  F2 = F^n_eq + c2 D
+//   R3 = F^n - k3 D - at32 X2                      F3 = R3 - a33 e3 D3
+//   R4 = F^n - k4 D - at42 X2 - a43 e3 D3 - at43 X3,  F4 = R4 - a44 e4 D4
+//   F^{n+1} = F^n - kf D - wt2 X2 - w3 e3 D3 - wt3 X3 - w4 e4 D4 - wt4 X4
+// where D_i = R_i - F^(i)_eq and F^(i)_eq has the moments of R_i (Sec. III).
+struct StageCoef {
+  double k3, k4, kf;            // weights of D in R3, R4 and F^{n+1}
+  double at32, at42, at43;      // explicit stage weights of X2, X3
+  double wt2, wt3, wt4;         // explicit final weights
+  double a33e3, a43e3, w3e3;    // weights of D3
+  double a44e4, w4e4;           // weights of D4
+  double c2;                    // F2 = F_eq + c2 (F - F_eq)
+};
+
+// Everything a stage kernel needs; passed by value as a __grid_constant__
+// kernel parameter (about 10 KB).
+struct DevParams {
+  int d, nx, ny, bc;            // dimension, cells, boundary condition
+  int Qp, Qc, P, nphi, nchi;    // lattice orders and population counts
+  int64_t N;                    // cells = nx * ny
+  double DK, kchi;              // D + K and D + K - d
+  double dtdx, dtdy;            // dt/dx, dt/dy
+  double pp[kMaxQ], pc[kMaxQ];  // phi and chi momenta (ascending)
+  double wHp[kMaxQ * kMaxQ];    // [l*kMaxQ + k] = w_k He_l(p_k)/l!, phi axis
+  double wHc[kMaxQ * kMaxQ];    // same for the chi axis
+  double invDK;                 // 1 / (D + K)
+  StageCoef sc;
+  // per population: dt p_x/dx, dt p_y/dy, p_x, p_y, and p^2 (phi) or 0 (chi)
+  double cx[kMaxPop], cy[kMaxPop], px[kMaxPop], py[kMaxPop], p2[kMaxPop];
+  double* F;    // state F^n (and F^{n+1} after the final stage)
+  double* F2;   // stage-2 populations (advected by stage 3)
+  double* F3;   // stage-3 populations (advected by stage 4); pass-1 scratch R3
+  double* A4;   // stage-4 explicit part, then F4 (advected by the final stage)
+  double* Af;   // running explicit part of F^{n+1}
+  double* D;    // F^n - F^n_eq
+  unsigned* status;  // bit 0: invalid moments seen
+};
+
+enum Stage { kPrep = 0, kStage3 = 1, kStage4 = 2, kFinal = 3 };
+
+// Kernel launchers (fdlb_kernels.cu).  Each returns a cudaError_t value.
+bool supported_lattice(int d, int Qp, int Qc);
+int launch_stage(const DevParams& p, int stage, cudaStream_t s);
+int launch_init_riemann(const DevParams& p, const double* states, int nq, double xsplit,
+                        double ysplit, double x0, double dx, double y0, double dy,
+                        cudaStream_t s);
+int launch_moments(const DevParams& p, double* n, double* ux, double* uy, double* T,
+                   cudaStream_t s);
+
+}  // namespace fdlb

@@ -1,0 +1,462 @@
+// fdlb_kernels.cu -- sm_103a kernels of the IMEX finite-difference lattice
+// Boltzmann step (Kis & Ambrus): one fused kernel per advected IMEX stage.
+//
+// Every stage kernel owns a tile of cells and all populations of those cells,
+// and runs two passes:
+//   pass 1  for each group of G populations: stage the advected array on the
+//           tile plus its 5-cell MP-9 halo in shared memory (ghosts by index
+//           clamp = outlet copies of the adjacent fluid node, Sec. IV), march
+//           every tile line computing each interface value once (MP-9 + MP
+//           limiter, fdlb_mp9.cuh), form the flux difference and the explicit
+//           part R_i of the stage (Eq. IMEX), accumulate the moments of R_i
+//           per cell (Eq. Moments_discrete) and park R_i and the running
+//           accumulators in the output arrays;
+//   pass 2  per cell: n, u, T from the moments, the Hermite equilibrium
+//           factors (Eq. gExpanded, recurrence form), and the closed-form
+//           implicit BGK relaxation of every population (Sec. III).
+// The flux itself never goes to global memory.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fdlb_internal.h"
+#include "fdlb_mp9.cuh"
+
+namespace fdlb {
+namespace {
+
+constexpr int H = 5;  // ghost nodes per side (Sec. IV)
+
+template <int DIM>
+struct TileCfg;
+// 2-D: 16 x 16 cells, 4 populations per group; 128 threads march the 4 x 32
+// tile lines (16 along x, 16 along y) of a group, one line each.
+template <>
+struct TileCfg<2> {
+  static constexpr int TX = 16, TY = 16, NT = 128, G = 4, SEG = TX + 1;
+};
+// 1-D: 127 cells, 8 populations per group; 128 threads march 16 segments of
+// 8 interfaces of each of the 8 lines.
+template <>
+struct TileCfg<1> {
+  static constexpr int TX = 127, TY = 1, NT = 128, G = 8, SEG = 8;
+};
+
+__device__ __forceinline__ int wrap_or_clamp(int i, int n, int bc) {
+  if (bc == 1) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+// One axis of the Hermite-expanded equilibrium (Eq. gExpanded):
+// g_k = sum_{l<Q} [w_k He_l(p_k)/l!] a_l(u, T) with
+// a_l = sum_s l!/(2^s s!(l-2s)!) (T-1)^s u^(l-2s), generated by the
+// recurrence a_0 = 1, a_1 = u, a_l = u a_{l-1} + (l-1)(T-1) a_{l-2}.
+// The nodes are antisymmetric (p_{Q-1-k} = -p_k, so He_l(p_{Q-1-k}) =
+// (-1)^l He_l(p_k)): g_k = E_k + O_k and g_{Q-1-k} = E_k - O_k with E/O the
+// even/odd-l partial sums.
+template <int Q>
+__device__ __forceinline__ void axis_g(const double* wH, double u, double T, double (&g)[Q]) {
+  double a[Q];
+  a[0] = 1.0;
+  if (Q > 1) a[1] = u;
+  const double tm1 = T - 1.0;
+#pragma unroll
+  for (int l = 2; l < Q; ++l) a[l] = fma(u, a[l - 1], ((double)(l - 1) * tm1) * a[l - 2]);
+#pragma unroll
+  for (int k = 0; k < (Q + 1) / 2; ++k) {
+    double e = wH[k];  // l = 0 (a_0 = 1)
+    double o = 0.0;
+#pragma unroll
+    for (int l = 1; l < Q; ++l) {
+      if (l & 1) o = fma(wH[l * kMaxQ + k], a[l], o);
+      else e = fma(wH[l * kMaxQ + k], a[l], e);
+    }
+    g[k] = e + o;
+    if (Q - 1 - k != k) g[Q - 1 - k] = e - o;
+  }
+}
+
+template <int DIM, int QP, int QC>
+struct Lat {
+  static constexpr int NPHI = DIM == 1 ? QP : QP * QP;
+  static constexpr int NCHI = DIM == 1 ? QC : QC * QC;
+  static constexpr int P = NPHI + NCHI;
+};
+
+struct Moments {
+  double n, jx, jy, e;
+};
+
+// phi: n += v, j += p v, e += p^2 v;  chi: e += v (Eq. Moments_discrete)
+template <int DIM, int QP, int QC>
+__device__ __forceinline__ void accumulate(const DevParams& p, Moments& m, int pop, double v) {
+  using L = Lat<DIM, QP, QC>;
+  if (pop < L::NPHI) {
+    m.n += v;
+    m.jx = fma(p.px[pop], v, m.jx);
+    if (DIM == 2) m.jy = fma(p.py[pop], v, m.jy);
+    m.e = fma(p.p2[pop], v, m.e);
+  } else {
+    m.e += v;
+  }
+}
+
+// Per-cell equilibrium factors: feq(phi kx,ky) = hp[kx] * gyp[ky],
+// feq(chi qx,qy) = hc[qx] * gyc[qy] (1-D: hp[kx], hc[qx]).
+template <int DIM, int QP, int QC>
+struct EqCell {
+  double hp[QP], gyp[DIM == 2 ? QP : 1];
+  double hc[QC], gyc[DIM == 2 ? QC : 1];
+};
+
+// Factors from (n, u, T); phi^eq = n prod g, chi^eq = (D+K-d) T n prod g^chi.
+template <int DIM, int QP, int QC>
+__device__ __forceinline__ void make_eq_nut(const DevParams& p, double n, double ux, double uy,
+                                            double T, EqCell<DIM, QP, QC>& eq) {
+  double gx[QP];
+  axis_g<QP>(p.wHp, ux, T, gx);
+#pragma unroll
+  for (int k = 0; k < QP; ++k) eq.hp[k] = n * gx[k];
+  if constexpr (DIM == 2) axis_g<QP>(p.wHp, uy, T, eq.gyp);
+  const double nchi = p.kchi * T * n;
+  if constexpr (QC == QP) {
+#pragma unroll
+    for (int k = 0; k < QC; ++k) eq.hc[k] = nchi * gx[k];
+    if constexpr (DIM == 2) {
+#pragma unroll
+      for (int k = 0; k < QC; ++k) eq.gyc[k] = eq.gyp[k];
+    }
+  } else {
+    double gc[QC];
+    axis_g<QC>(p.wHc, ux, T, gc);
+#pragma unroll
+    for (int k = 0; k < QC; ++k) eq.hc[k] = nchi * gc[k];
+    if constexpr (DIM == 2) axis_g<QC>(p.wHc, uy, T, eq.gyc);
+  }
+}
+
+// n, u and T = (sum phi p^2 + sum chi - n u^2) / ((D+K) n) from the moment
+// sums; false if the cell is not a valid gas state.
+template <int DIM>
+__device__ __forceinline__ bool moments_to_nut(const DevParams& p, const Moments& m, double& n,
+                                               double& ux, double& uy, double& T) {
+  n = m.n;
+  const double inv_n = 1.0 / n;
+  ux = m.jx * inv_n;
+  uy = DIM == 2 ? m.jy * inv_n : 0.0;
+  T = (m.e - n * fma(ux, ux, uy * uy)) * inv_n * p.invDK;
+  return (n > 0.0) && (T > 0.0) && isfinite(n) && isfinite(T) && isfinite(ux) && isfinite(uy);
+}
+
+template <int DIM, int QP, int QC>
+__device__ __forceinline__ double feq_of(const EqCell<DIM, QP, QC>& eq, int pop) {
+  using L = Lat<DIM, QP, QC>;
+  if (pop < L::NPHI) {
+    if constexpr (DIM == 1) return eq.hp[pop];
+    else return eq.hp[pop % QP] * eq.gyp[pop / QP];
+  }
+  const int q = pop - L::NPHI;
+  if constexpr (DIM == 1) return eq.hc[q];
+  else return eq.hc[q % QC] * eq.gyc[q / QC];
+}
+
+template <int DIM, int QP, int QC, int STAGE>
+__global__ void __launch_bounds__(TileCfg<DIM>::NT)
+    stage_kernel(const __grid_constant__ DevParams p) {
+  using C = TileCfg<DIM>;
+  using L = Lat<DIM, QP, QC>;
+  constexpr int TX = C::TX, TY = C::TY, NT = C::NT, G = C::G, SEG = C::SEG;
+  constexpr int SX = TX + 2 * H + (DIM == 2 ? 1 : 0);  // padded row pitch (2-D)
+  constexpr int SY = DIM == 2 ? TY + 2 * H : 1;
+  constexpr int CELLS = TX * TY;
+  constexpr int CPT = (CELLS + NT - 1) / NT;
+  constexpr int NSEG = (TX + 1) / SEG;  // segments per line
+  static_assert(NSEG * SEG == TX + 1, "segments tile the line");
+  constexpr int NLINE = DIM == 2 ? TX + TY : 1;
+  static_assert(G * NLINE * NSEG == NT, "one march task per thread");
+
+  __shared__ double tile[G][SY][SX];
+  __shared__ double hx[G][TY][TX + 1];
+  __shared__ double hy[DIM == 2 ? G : 1][DIM == 2 ? TX : 1][TY + 1];
+
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * TX;
+  const int y0 = blockIdx.y * TY;
+  const int64_t N = p.N;
+
+  int lxs[CPT], lys[CPT];
+  int64_t cell[CPT];
+  bool valid[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int c = tid + k * NT;
+    lxs[k] = c % TX;
+    lys[k] = c / TX;
+    const int x = x0 + lxs[k], y = y0 + lys[k];
+    valid[k] = (c < CELLS) && (x < p.nx) && (y < p.ny);
+    cell[k] = (int64_t)y * p.nx + x;
+  }
+  Moments mom[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) mom[k] = Moments{0.0, 0.0, 0.0, 0.0};
+
+  const StageCoef& sc = p.sc;
+
+  if (STAGE == kPrep) {
+    for (int pop = 0; pop < L::P; ++pop) {
+#pragma unroll
+      for (int k = 0; k < CPT; ++k)
+        if (valid[k]) accumulate<DIM, QP, QC>(p, mom[k], pop, p.F[pop * N + cell[k]]);
+    }
+  } else {
+    const double* __restrict__ adv = (STAGE == kStage3) ? p.F2 : (STAGE == kStage4) ? p.F3 : p.A4;
+    // this thread's march task: population tg of the group, line, segment
+    const int tg = tid / (NLINE * NSEG);
+    const int tline = (tid / NSEG) % NLINE;
+    const int tseg = tid % NSEG;
+    for (int g0 = 0; g0 < L::P; g0 += G) {
+      // ---- stage the advected populations of this group on tile + halo
+      for (int i = tid; i < G * SY * SX; i += NT) {
+        const int g = i / (SY * SX);
+        const int r = (i / SX) % SY;
+        const int cidx = i % SX;
+        const int pop = g0 + g;
+        double v = 0.0;
+        if (pop < L::P && cidx < TX + 2 * H) {
+          const int gx = wrap_or_clamp(x0 - H + cidx, p.nx, p.bc);
+          const int gy = (DIM == 2) ? wrap_or_clamp(y0 - H + r, p.ny, p.bc) : 0;
+          v = adv[pop * N + (int64_t)gy * p.nx + gx];
+        }
+        tile[g][r][cidx] = v;
+      }
+      __syncthreads();
+      // ---- every interface value once, marching upwind -> downwind
+      {
+        const int pop = g0 + tg;
+        const bool xline = (DIM == 1) || (tline < TY);
+        const double pv = (pop < L::P) ? (xline ? p.px[pop] : p.py[pop]) : 0.0;
+        const int sgn = (pv >= 0.0) ? 1 : -1;
+        const int i0 = tseg * SEG;  // first interface of the segment (low index)
+        // interface i lies between tile cells i-1 and i; its upwind cell is
+        // i-1 for p >= 0 and i for p < 0 (mirror image, index s+j <-> s+1-j);
+        // tile cell c sits at column/row c + H.
+        const int first = (sgn > 0) ? i0 : i0 + SEG - 1;
+        const int up = ((sgn > 0) ? first - 1 : first) + H;
+        if (xline) {
+          const int r = (DIM == 2) ? tline : 0;
+          mp9_march_fp64<SEG>(&tile[tg][r + (DIM == 2 ? H : 0)][up], sgn, &hx[tg][r][first], sgn);
+        } else {
+          const int c = tline - TY;
+          mp9_march_fp64<SEG>(&tile[tg][up][c + H], sgn * SX, &hy[tg][c][first], sgn);
+        }
+      }
+      __syncthreads();
+      // ---- flux difference, explicit part, moments (pass 1)
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        if (!valid[k]) continue;
+        const int lx = lxs[k], ly = lys[k];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int pop = g0 + g;
+          if (pop >= L::P) break;
+          // X = dt * (p . grad F) = dt p_x (Fhat_{x+1/2} - Fhat_{x-1/2})/dx + (y)
+          double X = p.cx[pop] * (hx[g][ly][lx + 1] - hx[g][ly][lx]);
+          if constexpr (DIM == 2) X = fma(p.cy[pop], hy[g][lx][ly + 1] - hy[g][lx][ly], X);
+          const int64_t e = pop * N + cell[k];
+          double R;
+          if (STAGE == kStage3) {
+            const double f = p.F[e], dd = p.D[e];
+            R = fma(-sc.at32, X, fma(-sc.k3, dd, f));
+            p.F3[e] = R;
+            p.A4[e] = fma(-sc.at42, X, fma(-sc.k4, dd, f));
+            p.Af[e] = fma(-sc.wt2, X, fma(-sc.kf, dd, f));
+          } else if (STAGE == kStage4) {
+            R = fma(-sc.at43, X, p.A4[e]);
+            p.A4[e] = R;
+            p.Af[e] = fma(-sc.wt3, X, p.Af[e]);
+          } else {  // kFinal: F^{n+1}
+            R = fma(-sc.wt4, X, p.Af[e]);
+            p.F[e] = R;
+          }
+          accumulate<DIM, QP, QC>(p, mom[k], pop, R);
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- pass 2: equilibrium of the moments and closed-form relaxation
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    if (!valid[k]) continue;
+    double n, ux, uy, T;
+    if (!moments_to_nut<DIM>(p, mom[k], n, ux, uy, T)) atomicOr(p.status, 1u);
+    EqCell<DIM, QP, QC> eq;
+    make_eq_nut<DIM, QP, QC>(p, n, ux, uy, T, eq);
+    const int64_t c = cell[k];
+#pragma unroll
+    for (int pop = 0; pop < L::P; ++pop) {
+      const int64_t e = pop * N + c;
+      const double fe = feq_of<DIM, QP, QC>(eq, pop);
+      if (STAGE == kStage3) {
+        const double R = p.F3[e];
+        const double D3 = R - fe;
+        p.F3[e] = fma(-sc.a33e3, D3, R);
+        p.A4[e] = fma(-sc.a43e3, D3, p.A4[e]);
+        p.Af[e] = fma(-sc.w3e3, D3, p.Af[e]);
+      } else if (STAGE == kStage4) {
+        const double R = p.A4[e];
+        const double D4 = R - fe;
+        p.A4[e] = fma(-sc.a44e4, D4, R);
+        p.Af[e] = fma(-sc.w4e4, D4, p.Af[e]);
+      } else {  // kPrep / kFinal: D and F2 of the new state
+        const double f = p.F[e];
+        const double dd = f - fe;
+        p.D[e] = dd;
+        p.F2[e] = fma(sc.c2, dd, fe);
+      }
+    }
+  }
+}
+
+// Piecewise-constant Riemann data -> discrete equilibrium (Sec. V).
+struct RiemannArgs {
+  double st[4][4];
+  int nq;
+  double xsplit, ysplit, x0, dx, y0, dy;
+};
+
+template <int DIM, int QP, int QC>
+__global__ void init_riemann_kernel(const __grid_constant__ DevParams p,
+                                    const __grid_constant__ RiemannArgs a) {
+  using L = Lat<DIM, QP, QC>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const int x = (int)(c % p.nx), y = (int)(c / p.nx);
+  const double xc = a.x0 + (x + 0.5) * a.dx;
+  int q;
+  if (DIM == 1) {
+    q = (xc >= a.xsplit) ? 1 : 0;
+  } else {
+    const double yc = a.y0 + (y + 0.5) * a.dy;
+    q = (yc >= a.ysplit) ? ((xc >= a.xsplit) ? 0 : 1) : ((xc >= a.xsplit) ? 3 : 2);
+  }
+  const double rho = a.st[q][0];
+  const double ux = a.st[q][1];
+  const double uy = DIM == 2 ? a.st[q][2] : 0.0;
+  const double P = a.st[q][DIM == 2 ? 3 : 2];
+  EqCell<DIM, QP, QC> eq;
+  make_eq_nut<DIM, QP, QC>(p, rho, ux, uy, P / rho, eq);
+#pragma unroll
+  for (int pop = 0; pop < L::P; ++pop) p.F[pop * p.N + c] = feq_of<DIM, QP, QC>(eq, pop);
+}
+
+template <int DIM, int QP, int QC>
+__global__ void moments_kernel(const __grid_constant__ DevParams p, double* __restrict__ n,
+                               double* __restrict__ ux, double* __restrict__ uy,
+                               double* __restrict__ T) {
+  using L = Lat<DIM, QP, QC>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  Moments m{0.0, 0.0, 0.0, 0.0};
+  for (int pop = 0; pop < L::P; ++pop) accumulate<DIM, QP, QC>(p, m, pop, p.F[pop * p.N + c]);
+  double nn, vx, vy, TT;
+  moments_to_nut<DIM>(p, m, nn, vx, vy, TT);
+  n[c] = nn;
+  ux[c] = vx;
+  if (DIM == 2 && uy) uy[c] = vy;
+  T[c] = TT;
+}
+
+template <int DIM, int QP, int QC>
+int launch_stage_t(const DevParams& p, int stage, cudaStream_t s) {
+  using C = TileCfg<DIM>;
+  dim3 grid((p.nx + C::TX - 1) / C::TX, DIM == 2 ? (p.ny + C::TY - 1) / C::TY : 1);
+  switch (stage) {
+    case kPrep: stage_kernel<DIM, QP, QC, kPrep><<<grid, C::NT, 0, s>>>(p); break;
+    case kStage3: stage_kernel<DIM, QP, QC, kStage3><<<grid, C::NT, 0, s>>>(p); break;
+    case kStage4: stage_kernel<DIM, QP, QC, kStage4><<<grid, C::NT, 0, s>>>(p); break;
+    default: stage_kernel<DIM, QP, QC, kFinal><<<grid, C::NT, 0, s>>>(p); break;
+  }
+  return (int)cudaGetLastError();
+}
+
+template <int DIM, int QP, int QC>
+int launch_init_t(const DevParams& p, const RiemannArgs& a, cudaStream_t s) {
+  const int nt = 128;
+  const int64_t nb = (p.N + nt - 1) / nt;
+  init_riemann_kernel<DIM, QP, QC><<<(unsigned)nb, nt, 0, s>>>(p, a);
+  return (int)cudaGetLastError();
+}
+
+template <int DIM, int QP, int QC>
+int launch_moments_t(const DevParams& p, double* n, double* ux, double* uy, double* T,
+                     cudaStream_t s) {
+  const int nt = 128;
+  const int64_t nb = (p.N + nt - 1) / nt;
+  moments_kernel<DIM, QP, QC><<<(unsigned)nb, nt, 0, s>>>(p, n, ux, uy, T);
+  return (int)cudaGetLastError();
+}
+
+// Dispatch over the compiled (d, Qphi, Qchi) instances.
+#define FDLB_LATTICES(X) \
+  X(1, 8, 8)             \
+  X(2, 8, 8)             \
+  X(1, 5, 3)             \
+  X(2, 5, 3)             \
+  X(1, 3, 3)             \
+  X(2, 3, 3)
+
+}  // namespace
+
+bool supported_lattice(int d, int Qp, int Qc) {
+#define X(D_, P_, C_) \
+  if (d == D_ && Qp == P_ && Qc == C_) return true;
+  FDLB_LATTICES(X)
+#undef X
+  return false;
+}
+
+int launch_stage(const DevParams& p, int stage, cudaStream_t s) {
+#define X(D_, P_, C_) \
+  if (p.d == D_ && p.Qp == P_ && p.Qc == C_) return launch_stage_t<D_, P_, C_>(p, stage, s);
+  FDLB_LATTICES(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_init_riemann(const DevParams& p, const double* states, int nq, double xsplit,
+                        double ysplit, double x0, double dx, double y0, double dy,
+                        cudaStream_t s) {
+  RiemannArgs a{};
+  const int w = p.d + 2;
+  for (int q = 0; q < nq && q < 4; ++q)
+    for (int j = 0; j < w; ++j) a.st[q][j] = states[q * w + j];
+  a.nq = nq;
+  a.xsplit = xsplit;
+  a.ysplit = ysplit;
+  a.x0 = x0;
+  a.dx = dx;
+  a.y0 = y0;
+  a.dy = dy;
+#define X(D_, P_, C_) \
+  if (p.d == D_ && p.Qp == P_ && p.Qc == C_) return launch_init_t<D_, P_, C_>(p, a, s);
+  FDLB_LATTICES(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_moments(const DevParams& p, double* n, double* ux, double* uy, double* T,
+                   cudaStream_t s) {
+#define X(D_, P_, C_) \
+  if (p.d == D_ && p.Qp == P_ && p.Qc == C_) return launch_moments_t<D_, P_, C_>(p, n, ux, uy, T, s);
+  FDLB_LATTICES(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace fdlb

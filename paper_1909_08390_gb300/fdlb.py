@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libfdlb.so (include/fdlb.h).
+
+Argument marshalling only: every step of the method runs in the library's
+sm_103a kernels.  The functions carry the C names (``fdlb_create``,
+``fdlb_init_riemann``, ``fdlb_step``, ``fdlb_moments``, ``fdlb_get_state``,
+``fdlb_set_state``, ``fdlb_destroy``, ...); ``Solver`` wraps a context for
+convenience.  Host arrays are numpy arrays; device arrays are torch CUDA
+tensors (PyTorch supplies device memory and streams).
+
+There is no fallback: if ``libfdlb.so`` is missing or cannot be loaded,
+``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfdlb.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "fdlb.h")
+
+FDLB_OK = 0
+FDLB_EINVAL = -1
+FDLB_ECFL = -2
+FDLB_ENOMEM = -3
+FDLB_ECUDA = -4
+FDLB_EUNSTABLE = -5
+FDLB_ETIMEOUT = -6
+FDLB_FP64 = 0
+FDLB_MIXED = 1
+FDLB_BC_OUTLET = 0
+FDLB_BC_PERIODIC = 1
+
+_ERRNAMES = {0: "FDLB_OK", -1: "FDLB_EINVAL", -2: "FDLB_ECFL", -3: "FDLB_ENOMEM",
+             -4: "FDLB_ECUDA", -5: "FDLB_EUNSTABLE", -6: "FDLB_ETIMEOUT"}
+
+
+class fdlb_grid(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("bc", ctypes.c_int)]
+
+
+class fdlb_tableau(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int), ("At", ctypes.c_double * 16), ("A", ctypes.c_double * 16),
+                ("wt", ctypes.c_double * 4), ("w", ctypes.c_double * 4)]
+
+
+class FdlbError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libfdlb.so (built by ``paper_1909_08390_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FdlbError(FDLB_ECUDA, f"{path} not built; run paper_1909_08390_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    lib.fdlb_create.argtypes = [ctypes.POINTER(fdlb_grid), ctypes.c_int, ctypes.c_int,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.POINTER(fdlb_tableau), ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+    lib.fdlb_create.restype = ctypes.c_int
+    lib.fdlb_init_riemann.argtypes = [_vp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lib.fdlb_step.argtypes = [_vp, ctypes.c_int64]
+    lib.fdlb_step_timed.argtypes = [_vp, ctypes.c_int64, _dp]
+    lib.fdlb_moments.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+    lib.fdlb_state_bytes.argtypes = [_vp]
+    lib.fdlb_state_bytes.restype = ctypes.c_size_t
+    lib.fdlb_get_state.argtypes = [_vp, _vp, ctypes.c_int]
+    lib.fdlb_set_state.argtypes = [_vp, _vp, ctypes.c_int]
+    lib.fdlb_npop.argtypes = [_vp]
+    lib.fdlb_ncells.argtypes = [_vp]
+    lib.fdlb_ncells.restype = ctypes.c_int64
+    lib.fdlb_set_stream.argtypes = [_vp, _vp]
+    lib.fdlb_launches_per_step.argtypes = [_vp]
+    lib.fdlb_lattice_nodes.argtypes = [ctypes.c_int, _dp, _dp]
+    lib.fdlb_destroy.argtypes = [_vp]
+    lib.fdlb_destroy.restype = None
+    lib.fdlb_last_error.argtypes = [_vp]
+    lib.fdlb_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def header_symbols(path: str = HEADER):
+    """Names of the functions include/fdlb.h declares."""
+    with open(path) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdlb_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(rc: int, ctx=None):
+    if rc != FDLB_OK:
+        msg = load().fdlb_last_error(ctx).decode()
+        raise FdlbError(rc, msg)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- functions with the C names -------------------------------------------
+
+def fdlb_create(grid: fdlb_grid, Qphi: int, Qchi: int, gamma: float, tau: float, dt: float,
+                tableau: fdlb_tableau | None = None, precision: int = FDLB_FP64, stream=None):
+    lib = load()
+    out = _vp()
+    tab = ctypes.byref(tableau) if tableau is not None else None
+    rc = lib.fdlb_create(ctypes.byref(grid), int(Qphi), int(Qchi), float(gamma), float(tau),
+                         float(dt), tab, int(precision), _stream_handle(stream), ctypes.byref(out))
+    _check(rc, None)
+    return out
+
+
+def fdlb_init_riemann(ctx, states, xsplit: float, ysplit: float = 0.0):
+    st = np.ascontiguousarray(states, dtype=np.float64)
+    _check(load().fdlb_init_riemann(ctx, st.ctypes.data_as(_dp), st.shape[0], float(xsplit),
+                                    float(ysplit)), ctx)
+
+
+def fdlb_step(ctx, nsteps: int):
+    _check(load().fdlb_step(ctx, int(nsteps)), ctx)
+
+
+def fdlb_step_timed(ctx, nsteps: int):
+    """Returns the summed device ms of the stage-3, stage-4 and final kernels."""
+    ms = (ctypes.c_double * 3)()
+    _check(load().fdlb_step_timed(ctx, int(nsteps), ms), ctx)
+    return [ms[0], ms[1], ms[2]]
+
+
+def fdlb_moments(ctx, n, ux, uy, T, on_device: bool):
+    ptr = (lambda a: None if a is None else (a.data_ptr() if on_device else a.ctypes.data))
+    _check(load().fdlb_moments(ctx, ptr(n), ptr(ux), ptr(uy), ptr(T), int(on_device)), ctx)
+
+
+def fdlb_state_bytes(ctx) -> int:
+    return int(load().fdlb_state_bytes(ctx))
+
+
+def fdlb_get_state(ctx, dst, on_device: bool):
+    ptr = dst.data_ptr() if on_device else dst.ctypes.data
+    _check(load().fdlb_get_state(ctx, ptr, int(on_device)), ctx)
+
+
+def fdlb_set_state(ctx, src, on_device: bool):
+    ptr = src.data_ptr() if on_device else src.ctypes.data
+    _check(load().fdlb_set_state(ctx, ptr, int(on_device)), ctx)
+
+
+def fdlb_npop(ctx) -> int:
+    return int(load().fdlb_npop(ctx))
+
+
+def fdlb_ncells(ctx) -> int:
+    return int(load().fdlb_ncells(ctx))
+
+
+def fdlb_set_stream(ctx, stream):
+    _check(load().fdlb_set_stream(ctx, _stream_handle(stream)), ctx)
+
+
+def fdlb_launches_per_step(ctx) -> int:
+    return int(load().fdlb_launches_per_step(ctx))
+
+
+def fdlb_lattice_nodes(Q: int):
+    p = np.zeros(Q)
+    w = np.zeros(Q)
+    _check(load().fdlb_lattice_nodes(int(Q), p.ctypes.data_as(_dp), w.ctypes.data_as(_dp)), None)
+    return p, w
+
+
+def fdlb_destroy(ctx):
+    if ctx:
+        load().fdlb_destroy(ctx)
+
+
+def fdlb_last_error(ctx=None) -> str:
+    return load().fdlb_last_error(ctx).decode()
+
+
+def make_tableau(At, A, wt, w) -> fdlb_tableau:
+    t = fdlb_tableau()
+    r = len(w)
+    t.r = r
+    for i in range(r):
+        for j in range(r):
+            t.At[i * r + j] = At[i][j]
+            t.A[i * r + j] = A[i][j]
+        t.wt[i] = wt[i]
+        t.w[i] = w[i]
+    return t
+
+
+# ---- convenience wrapper ---------------------------------------------------
+
+class Solver:
+    """One library context.  ``Solver.from_workload(wl)`` builds it from a
+    ``workloads.Workload``."""
+
+    def __init__(self, d: int, nx: int, ny: int = 1, x0: float = -0.5, x1: float = 0.5,
+                 y0: float = 0.0, y1: float = 1.0, bc: int = FDLB_BC_OUTLET, Qphi: int = 8,
+                 Qchi: int = 8, gamma: float = 1.4, tau: float = 1e-6, dt: float = 5e-5,
+                 tableau: fdlb_tableau | None = None, precision: int = FDLB_FP64, stream=None):
+        g = fdlb_grid(d, nx, ny if d == 2 else 1, x0, x1, y0, y1, bc)
+        self.d, self.nx, self.ny = d, nx, (ny if d == 2 else 1)
+        self.ctx = fdlb_create(g, Qphi, Qchi, gamma, tau, dt, tableau, precision, stream)
+        self.P = fdlb_npop(self.ctx)
+        self.N = fdlb_ncells(self.ctx)
+
+    @classmethod
+    def from_workload(cls, wl, precision: int = FDLB_FP64, stream=None, **kw):
+        args = dict(d=wl.d, nx=wl.nx, ny=wl.ny, x0=wl.x0, x1=wl.x1, y0=wl.y0, y1=wl.y1, bc=wl.bc,
+                    Qphi=wl.Qphi, Qchi=wl.Qchi, gamma=wl.gamma, tau=wl.tau, dt=wl.dt)
+        args.update(kw)
+        return cls(precision=precision, stream=stream, **args)
+
+    @property
+    def shape(self):
+        return (self.P, self.ny, self.nx) if self.d == 2 else (self.P, self.nx)
+
+    def init_riemann(self, states, xsplit: float, ysplit: float = 0.0):
+        fdlb_init_riemann(self.ctx, states, xsplit, ysplit)
+
+    def step(self, nsteps: int = 1):
+        fdlb_step(self.ctx, nsteps)
+
+    def state(self) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.float64)
+        fdlb_get_state(self.ctx, out, False)
+        return out
+
+    def set_state(self, F):
+        if hasattr(F, "data_ptr"):
+            fdlb_set_state(self.ctx, F, True)
+        else:
+            F = np.ascontiguousarray(F, dtype=np.float64)
+            assert F.size == self.P * self.N
+            fdlb_set_state(self.ctx, F, False)
+
+    def moments(self):
+        sh = self.shape[1:]
+        n, ux, T = (np.empty(sh) for _ in range(3))
+        uy = np.empty(sh) if self.d == 2 else None
+        fdlb_moments(self.ctx, n, ux, uy, T, False)
+        return n, ux, uy, T
+
+    def close(self):
+        if self.ctx:
+            fdlb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -75,6 +75,12 @@ def sod_1d(nx: int = 400, Q: int = 8, Qchi: int | None = None, gamma: float = 1.
                     gamma, tau, dt, t_end, (SOD_LEFT, SOD_RIGHT), 0.0, 0.0)
 
 
+# Seed of the 512 x 512 benchmark problem: the first seed whose four quadrant
+# states the scheme carries to t = 0.25 without a cell reaching T <= 0 on a
+# coarse grid (seeds 0 and 3 do not; see quadrant_2d).
+BENCH_SEED = 1
+
+
 def quadrant_states(seed: int) -> tuple:
     rng = np.random.default_rng(seed)
     out = []
@@ -158,3 +164,21 @@ def smooth_fields_2d(n: int, seed: int = 0, amp: float = 0.1):
 def random_populations(shape, seed: int = 0, lo: float = 0.5, hi: float = 1.5) -> np.ndarray:
     """Uniform random population values (for element-wise kernel checks)."""
     return np.random.default_rng(seed).uniform(lo, hi, size=shape)
+
+
+def smooth_random_populations(shape, seed: int = 0, amp: float = 0.2) -> np.ndarray:
+    """Positive populations, each a constant plus a few random low Fourier modes
+    along every axis of the grid (for parity checks away from equilibrium)."""
+    rng = np.random.default_rng(seed)
+    P, grid = shape[0], shape[1:]
+    out = np.empty(shape)
+    axes = [(np.arange(n) + 0.5) / n for n in grid]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    for k in range(P):
+        f = np.full(grid, rng.uniform(0.5, 1.5))
+        for _ in range(3):
+            phase = rng.uniform(0, 2 * math.pi)
+            arg = sum(int(rng.integers(0, 3)) * 2 * math.pi * m for m in mesh)
+            f = f + amp * rng.uniform(-1, 1) * np.cos(arg + phase)
+        out[k] = f
+    return out
