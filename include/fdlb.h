@@ -149,6 +149,34 @@ int fdlb_launches_per_step(const fdlb_ctx* ctx);
  * needed.  Returns FDLB_EINVAL for Q out of range or NULL arrays. */
 int fdlb_lattice_nodes(int Q, double* p, double* w);
 
+/* Size of the static device scratch array used by fdlb_step_noalloc. */
+#define FDLB_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* fdlb_step_noalloc -- advance a caller-owned binary64 state by nsteps IMEX
+ * steps without allocating any memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, e.g. code
+ * running inside another framework whose pool allocator owns all device
+ * memory, or a real-time loop that may not take an allocation's latency and
+ * device-wide synchronisation.
+ *   grid, Qphi, Qchi, gamma, tau, dt, tableau : as for fdlb_create
+ *   F          : device pointer to the state, layout F[P][ny][nx] (binary64),
+ *                read as the initial state and overwritten with the result
+ *   nsteps     : >= 0
+ *   cuda_stream: stream to enqueue on (NULL: legacy default stream)
+ * The intermediate arrays live in one static __device__ array of
+ * FDLB_NOALLOC_SCRATCH_BYTES (64 MiB), which every GPU that loads the
+ * library keeps until the process exits; problems with 5 * P * cells * 8 >
+ * 64 MiB - 256 bytes are rejected with FDLB_EINVAL.  No cudaMalloc, cudaFree
+ * or other allocating routine is called.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.  All calls share the array: two
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * and corrupt each other.  The call synchronises its stream to read the
+ * status word; errors are reported through fdlb_last_error(NULL). */
+int fdlb_step_noalloc(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double tau,
+                      double dt, const fdlb_tableau* tableau, double* F, int64_t nsteps,
+                      void* cuda_stream);
+
 /* Release the context and its device buffers (NULL is a no-op). */
 void fdlb_destroy(fdlb_ctx* ctx);
 

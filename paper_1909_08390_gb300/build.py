@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdlb.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-SOURCES = ["fdlb_kernels.cu", "fdlb_api.cpp"]
+SOURCES = ["fdlb_kernels.cu", "fdlb_api.cpp", "fdlb_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "fdlb_internal.h"), os.path.join(INCLUDE, "fdlb.h")]
 
 

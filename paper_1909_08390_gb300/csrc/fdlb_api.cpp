@@ -209,6 +209,91 @@ int ensure_prepared(fdlb_ctx* c) {
 
 }  // namespace
 
+namespace fdlb {
+
+// Constants of a DevParams (lattice, grid, stage coefficients; the buffer
+// pointers are left alone) for the arguments of fdlb_create, with the same
+// checks.  Used by the allocation-free entry point (fdlb_noalloc.cu).
+int params_for(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double tau, double dt,
+               const fdlb_tableau* tableau, DevParams* out) {
+  if (!grid || !out) return set_err(nullptr, FDLB_EINVAL, "grid or params is NULL");
+  const fdlb_grid& g = *grid;
+  if (g.d != 1 && g.d != 2) return set_err(nullptr, FDLB_EINVAL, "d must be 1 or 2 (got %d)", g.d);
+  const int64_t ny = (g.d == 2) ? g.ny : 1;
+  if (g.nx < 1 || ny < 1 || g.nx > (1 << 30) || ny > (1 << 30))
+    return set_err(nullptr, FDLB_EINVAL, "bad cell counts nx=%lld ny=%lld", (long long)g.nx,
+                   (long long)g.ny);
+  if (!(g.x1 > g.x0) || (g.d == 2 && !(g.y1 > g.y0)))
+    return set_err(nullptr, FDLB_EINVAL, "empty domain");
+  if (g.bc != FDLB_BC_OUTLET && g.bc != FDLB_BC_PERIODIC)
+    return set_err(nullptr, FDLB_EINVAL, "bc must be 0 (outlet) or 1 (periodic)");
+  if (!supported_lattice(g.d, Qphi, Qchi))
+    return set_err(nullptr, FDLB_EINVAL, "lattice d=%d Qphi=%d Qchi=%d not compiled", g.d, Qphi,
+                   Qchi);
+  if (!(gamma > 1.0) || !std::isfinite(gamma))
+    return set_err(nullptr, FDLB_EINVAL, "gamma must be > 1");
+  const double DK = 2.0 / (gamma - 1.0);
+  if (DK - g.d < 0.0)
+    return set_err(nullptr, FDLB_EINVAL, "gamma=%g gives D+K-d=%g < 0", gamma, DK - g.d);
+  if (!(tau > 0.0) || !(dt > 0.0) || !std::isfinite(tau) || !std::isfinite(dt))
+    return set_err(nullptr, FDLB_EINVAL, "tau and dt must be positive");
+  fdlb_tableau tab;
+  if (tableau) tab = *tableau;
+  else paper_tableau(&tab);
+  DevParams& p = *out;
+  p.d = g.d;
+  p.nx = (int)g.nx;
+  p.ny = (int)ny;
+  p.bc = g.bc;
+  p.Qp = Qphi;
+  p.Qc = Qchi;
+  p.nphi = g.d == 1 ? Qphi : Qphi * Qphi;
+  p.nchi = g.d == 1 ? Qchi : Qchi * Qchi;
+  p.P = p.nphi + p.nchi;
+  p.N = g.nx * ny;
+  p.DK = DK;
+  p.kchi = DK - g.d;
+  const double dx = (g.x1 - g.x0) / (double)g.nx;
+  const double dy = (g.d == 2) ? (g.y1 - g.y0) / (double)ny : 1.0;
+  p.dtdx = dt / dx;
+  p.dtdy = (g.d == 2) ? dt / dy : 0.0;
+  double wp[kMaxQ], wc[kMaxQ];
+  if (!gauss_hermite(Qphi, p.pp, wp) || !gauss_hermite(Qchi, p.pc, wc))
+    return set_err(nullptr, FDLB_EINVAL, "Gauss-Hermite rule failed to converge");
+  weighted_hermite_table(Qphi, p.pp, wp, p.wHp);
+  weighted_hermite_table(Qchi, p.pc, wc, p.wHc);
+  const double pmax = std::fmax(std::fabs(p.pp[Qphi - 1]), std::fabs(p.pc[Qchi - 1]));
+  const double cfl = pmax * std::fmax(p.dtdx, p.dtdy);
+  if (cfl > 1.0) return set_err(nullptr, FDLB_ECFL, "CFL = %g > 1", cfl);
+  p.invDK = 1.0 / DK;
+  for (int pop = 0; pop < p.P; ++pop) {
+    double ax, ay;
+    if (pop < p.nphi) {
+      ax = p.pp[g.d == 1 ? pop : pop % Qphi];
+      ay = g.d == 1 ? 0.0 : p.pp[pop / Qphi];
+      p.p2[pop] = ax * ax + ay * ay;
+    } else {
+      const int q = pop - p.nphi;
+      ax = p.pc[g.d == 1 ? q : q % Qchi];
+      ay = g.d == 1 ? 0.0 : p.pc[q / Qchi];
+      p.p2[pop] = 0.0;
+    }
+    p.px[pop] = ax;
+    p.py[pop] = ay;
+    p.cx[pop] = p.dtdx * ax;
+    p.cy[pop] = p.dtdy * ay;
+  }
+  const char* why = nullptr;
+  if (!stage_coefficients(tab, dt / tau, &p.sc, &why))
+    return set_err(nullptr, FDLB_EINVAL, "unsupported tableau: %s", why);
+  return FDLB_OK;
+}
+
+// Record a context-less error for fdlb_last_error(NULL).
+int record_error(int code, const char* msg) { return set_err(nullptr, code, "%s", msg); }
+
+}  // namespace fdlb
+
 extern "C" {
 
 int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double tau, double dt,

@@ -86,6 +86,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fdlb_set_stream.argtypes = [_vp, _vp]
     lib.fdlb_launches_per_step.argtypes = [_vp]
     lib.fdlb_lattice_nodes.argtypes = [ctypes.c_int, _dp, _dp]
+    lib.fdlb_step_noalloc.argtypes = [ctypes.POINTER(fdlb_grid), ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.POINTER(fdlb_tableau), _vp, ctypes.c_int64, _vp]
     lib.fdlb_destroy.argtypes = [_vp]
     lib.fdlb_destroy.restype = None
     lib.fdlb_last_error.argtypes = [_vp]
@@ -192,6 +195,18 @@ def fdlb_lattice_nodes(Q: int):
     w = np.zeros(Q)
     _check(load().fdlb_lattice_nodes(int(Q), p.ctypes.data_as(_dp), w.ctypes.data_as(_dp)), None)
     return p, w
+
+
+def fdlb_step_noalloc(grid: fdlb_grid, Qphi: int, Qchi: int, gamma: float, tau: float,
+                      dt: float, F, nsteps: int, tableau: fdlb_tableau | None = None,
+                      stream=None):
+    """Advance the device state F (a torch CUDA float64 tensor, updated in
+    place) by nsteps steps with the library's static scratch (no allocation)."""
+    tab = ctypes.byref(tableau) if tableau is not None else None
+    rc = load().fdlb_step_noalloc(ctypes.byref(grid), int(Qphi), int(Qchi), float(gamma),
+                                  float(tau), float(dt), tab, F.data_ptr(), int(nsteps),
+                                  _stream_handle(stream))
+    _check(rc, None)
 
 
 def fdlb_destroy(ctx):
