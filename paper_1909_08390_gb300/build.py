@@ -2,8 +2,8 @@
 
 The kernels (csrc/fdlb_kernels.cu) go through nvcc with a single
 ``-gencode arch=compute_103a,code=sm_103a``; the host API (csrc/fdlb_api.cpp)
-through g++; both compile in parallel and are linked by nvcc with the static
-CUDA runtime.  Objects go to ``_build/`` next to this file.
+through g++; both compile in parallel and are linked by nvcc against the shared CUDA
+runtime (the one PyTorch loads), so device selection and streams are shared.  Objects go to ``_build/`` next to this file.
 """
 from __future__ import annotations
 
@@ -73,7 +73,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError("libfdlb build failed")
     if force or _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.run([nvcc, ARCH, "-shared", "-o", tmp] + objs, check=True)
+        # the shared CUDA runtime: one runtime instance per process, so the
+        # library sees the device and streams PyTorch selected
+        lib64 = os.path.join(cuda, "lib64")
+        subprocess.run([nvcc, ARCH, "-shared", "-cudart", "shared", "-Xlinker", "-rpath",
+                        "-Xlinker", lib64, "-o", tmp] + objs, check=True)
         os.replace(tmp, LIB)
     return LIB
 

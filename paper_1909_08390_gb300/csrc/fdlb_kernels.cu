@@ -245,13 +245,14 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
         // tile cell c sits at column/row c + H.
         const int first = (sgn > 0) ? i0 : i0 + SEG - 1;
         const int up = ((sgn > 0) ? first - 1 : first) + H;
-        if (xline) {
-          const int r = (DIM == 2) ? tline : 0;
-          mp9_march_fp64<SEG>(&tile[tg][r + (DIM == 2 ? H : 0)][up], sgn, &hx[tg][r][first], sgn);
-        } else {
-          const int c = tline - TY;
-          mp9_march_fp64<SEG>(&tile[tg][up][c + H], sgn * SX, &hy[tg][c][first], sgn);
-        }
+        // one call site for x and y lines (a warp holds both kinds): the line
+        // is (base, element stride) in the tile and its output row
+        const int r = (DIM == 2 && xline) ? tline : 0;  // x line: tile row
+        const int c = xline ? 0 : tline - TY;           // y line: tile column
+        const double* base = xline ? &tile[tg][r + (DIM == 2 ? H : 0)][up] : &tile[tg][up][c + H];
+        const int stride = xline ? 1 : SX;
+        double* out = xline ? &hx[tg][r][first] : &hy[tg][c][first];
+        mp9_march_fp64<SEG>(base, sgn * stride, out, sgn);
       }
       __syncthreads();
       // ---- flux difference, explicit part, moments (pass 1)

@@ -4,19 +4,32 @@
 // On GB300 the binary64 pipe issues two lanes per clock per SM, 64 times
 // fewer than binary32, so the binary64 path spends that pipe on additions and
 // multiplications only.  Every comparison, min/max, sign test, absolute
-// value and selection of the limiter runs on the integer pipe on the bit
-// patterns: for IEEE doubles, k(x) = bits(x) ^ ((bits(x) >> 63) & 0x7ff..f)
-// is strictly increasing in x (with -0 ordered just below +0), so
-// min/max/median of doubles are min/max/median of these int64 keys, and the
-// key map is its own inverse.
+// value, power-of-two scaling and selection of the limiter runs on the
+// integer pipe on the bit patterns: for IEEE doubles, k(x) = bits(x) ^
+// ((bits(x) >> 63) & 0x7ff..f) is strictly increasing in x (with -0 ordered
+// just below +0), so min/max/median of doubles are min/max/median of these
+// int64 keys, and the key map is its own inverse.
 //
-// The linear 9-point value is written on forward differences
-// d_k = F_{s+k+1} - F_{s+k} (k = -4..3, s the upwind cell):
-//   F^L - F_s = (-4 d_-4 + 37 d_-3 - 162 d_-2 + 479 d_-1 + 1120 d_0
-//                - 255 d_1 + 50 d_2 - 5 d_3) / 2520,
-// which is the printed stencil (coefficients 4, -41, 199, -641, 1879, 1375,
-// -305, 55, -5 over 2520) summed by parts.  Marching along a line, each
-// difference is computed once and slides through registers.
+// Formulation (all quantities are offsets from the upwind value F_s):
+//   d_k  = F_{s+k+1} - F_{s+k}, k = -4..3        (forward differences)
+//   a    = F^L - F_s = (-4 d_-4 + 37 d_-3 - 162 d_-2 + 479 d_-1 + 1120 d_0
+//                       - 255 d_1 + 50 d_2 - 5 d_3) / 2520
+//          (the printed 9-point stencil 4, -41, 199, -641, 1879, 1375, -305,
+//          55, -5 over 2520, summed by parts)
+//   C_j  = d_j - d_{j-1}                           (curvatures C_s, C_{s+-1})
+//   DM+  = minmod4(4C_s - C_{s+1}, 4C_{s+1} - C_s, C_s, C_{s+1}), DM- likewise
+//          with C_{s-1}; DM- of one interface is DM+ of the previous one
+//   F^UL - F_s = 4 d_-1,  F^MD - F_s = (d_0 - DM+)/2,
+//   F^LC - F_s = d_-1/2 + (4/3) DM-,  F_{s+1} - F_s = d_0
+//   lo = max(min(0, d_0, md), min(0, ul, lc)), hi = min(max(0, d_0, md), max(0, ul, lc))
+//   Fhat = F_s + clamp(a, lo, hi).
+// The last line equals the paper's two cases: when (F^L - F_s)(F^L - F^MP) <=
+// 0, a lies between 0 and minmod(d_0, 4 d_-1), an interval inside [lo, hi],
+// so the clamp returns a; otherwise F^L + minmod(F^min - F^L, F^max - F^L) is
+// F^L clamped to [F^min, F^max].  Evaluating it without the test keeps the
+// warps of a line together (most lines of a developed flow have limited
+// interfaces).  The bounds are formed at twice their value so that every
+// halving becomes an exact power-of-two scaling.
 #pragma once
 
 #include <cstdint>
@@ -26,6 +39,7 @@ namespace fdlb {
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ double dfrom(long long b) { return __longlong_as_double(b); }
 constexpr long long kMag = 0x7fffffffffffffffLL;
+constexpr long long kSign = (long long)0x8000000000000000ULL;
 
 // order-preserving integer key (self-inverse)
 __device__ __forceinline__ long long okey(long long b) { return b ^ ((b >> 63) & kMag); }
@@ -46,16 +60,20 @@ __device__ __forceinline__ long long minmod4_bits(long long a, long long b, long
   return (same && nz) ? r : 0;
 }
 
-// |4x| as a magnitude bit pattern (x = +-0 gives 0).  Exact for normal x with
-// |x| < 2^1021; below the normal range the pattern is shifted (4x exactly
-// while |x| < 2^-1073), above it saturates -- magnitudes populations of a
-// valid state never take.
-__device__ __forceinline__ long long mag_times4(long long b) {
+// bits of x * 2^K, K = 1..3, as an ordering key.  Exact for normal x with
+// |x| < 2^(1024-K); zero stays zero; below the normal range the magnitude
+// pattern is shifted (x * 2^K exactly while the result stays subnormal),
+// above it saturates -- magnitudes that population differences of a valid
+// state never take.
+template <int K>
+__device__ __forceinline__ long long key_times_pow2(long long b) {
   const long long m = b & kMag;
   const long long e = m >> 52;
-  if (e == 0) return m << 2;
-  if (e > 2044) return 0x7fefffffffffffffLL;
-  return m + (2LL << 52);
+  long long r;
+  if (e == 0) r = m << K;
+  else if (e > 2046 - K) r = 0x7fefffffffffffffLL;
+  else r = m + ((long long)K << 52);
+  return okey(r | (b & kSign));
 }
 
 struct Mp9Coef {
@@ -65,10 +83,21 @@ struct Mp9Coef {
                           b6 = 50.0 / 2520.0, b7 = -5.0 / 2520.0;
 };
 
-// Interface value from the window v[0..8] = F_{s-4..s+4} (upwind
-// orientation) and its differences d[0..7] = F_{s-3..s+4} - F_{s-4..s+3}.
-__device__ __forceinline__ double mp9_face_fp64(const double (&v)[9], const double (&d)[8]) {
+// Sliding state of one line: the upwind value F_s, the newest value, the
+// eight differences d_-4..d_3, the curvatures C_{s-1}, C_s and DM- (the DM+
+// of the previous interface).
+struct Mp9Line {
+  double fs[5];  // F_s .. F_{s+4}
+  double d[8];   // d_-4 .. d_3
+  double cm1, c0;
+  long long dmm;
+};
+
+// Interface value for the current window; advances nothing.
+__device__ __forceinline__ double mp9_face_fp64(const Mp9Line& L, double& c1_out,
+                                                long long& dmp_out) {
   using B = Mp9Coef;
+  const double* d = L.d;
   double a = B::b0 * d[0];
   a = fma(B::b1, d[1], a);
   a = fma(B::b2, d[2], a);
@@ -77,58 +106,60 @@ __device__ __forceinline__ double mp9_face_fp64(const double (&v)[9], const doub
   a = fma(B::b5, d[5], a);
   a = fma(B::b6, d[6], a);
   a = fma(B::b7, d[7], a);
-  const double Fs = v[4];
-  const double FL = Fs + a;
-  // (F^L - F_s)(F^L - F^MP) <= 0 with F^MP = F_s + minmod(d_0, 4 d_-1), i.e.
-  // a lies between 0 and minmod(d_0, 4 d_-1) (both inclusive): keep F^L.
-  const long long ba = dbits(a), b0 = dbits(d[4]), bm = dbits(d[3]);
-  const long long ma = ba & kMag, m0 = b0 & kMag, mm = bm & kMag;
-  const bool keep = (ma == 0) || (((b0 ^ bm) >= 0) && (m0 != 0) && (mm != 0) &&
-                                  ((ba ^ b0) >= 0) && (ma <= m0) && (ma <= mag_times4(bm)));
-  if (keep) return FL;
-  // limited branch: curvatures, bounds, and the median
-  const double Cm1 = d[3] - d[2];  // C_{s-1} = F_s - 2F_{s-1} + F_{s-2}
-  const double C0 = d[4] - d[3];   // C_s
-  const double Cp1 = d[5] - d[4];  // C_{s+1}
-  const long long dmp = minmod4_bits(dbits(fma(4.0, C0, -Cp1)), dbits(fma(4.0, Cp1, -C0)),
-                                     dbits(C0), dbits(Cp1));
-  const long long dmm = minmod4_bits(dbits(fma(4.0, C0, -Cm1)), dbits(fma(4.0, Cm1, -C0)),
-                                     dbits(C0), dbits(Cm1));
-  const double FUL = fma(4.0, d[3], Fs);                          // F_s + 4 (F_s - F_{s-1})
-  const double FMD = fma(0.5, d[4] - dfrom(dmp), Fs);             // (F_s + F_{s+1} - DM+)/2
-  const double FLC = fma(4.0 / 3.0, dfrom(dmm), fma(0.5, d[3], Fs));
-  const long long kFs = okey(dbits(Fs)), kFp1 = okey(dbits(v[5])), kMD = okey(dbits(FMD));
-  const long long kUL = okey(dbits(FUL)), kLC = okey(dbits(FLC));
-  const long long kmin1 = kmin(kFs, kmin(kFp1, kMD)), kmin2 = kmin(kFs, kmin(kUL, kLC));
-  const long long kmax1 = kmax(kFs, kmax(kFp1, kMD)), kmax2 = kmax(kFs, kmax(kUL, kLC));
-  const long long klo = kmax(kmin1, kmin2), khi = kmin(kmax1, kmax2);  // klo <= k(F_s) <= khi
-  // F^L + minmod(F^min - F^L, F^max - F^L) = F^L clamped to [F^min, F^max]
-  const long long kFL = okey(dbits(FL));
-  return dfrom(okey(kmin(kmax(kFL, klo), khi)));
+  const double c1 = d[5] - d[4];  // C_{s+1}
+  const double c0 = L.c0;
+  const long long dmp = minmod4_bits(dbits(fma(4.0, c0, -c1)), dbits(fma(4.0, c1, -c0)),
+                                     dbits(c0), dbits(c1));
+  // bounds at twice their value: 2 d_0, 2 md = d_0 - DM+, 2 ul = 8 d_-1,
+  // 2 lc = d_-1 + (8/3) DM-, and 2a
+  const long long k_d0 = key_times_pow2<1>(dbits(d[4]));
+  const long long k_md = okey(dbits(d[4] - dfrom(dmp)));
+  const long long k_ul = key_times_pow2<3>(dbits(d[3]));
+  const long long k_lc = okey(dbits(fma(8.0 / 3.0, dfrom(L.dmm), d[3])));
+  const long long k_a = key_times_pow2<1>(dbits(a));
+  const long long lo = kmax(kmin(0, kmin(k_d0, k_md)), kmin(0, kmin(k_ul, k_lc)));
+  const long long hi = kmin(kmax(0, kmax(k_d0, k_md)), kmax(0, kmax(k_ul, k_lc)));
+  const double r2 = dfrom(okey(kmin(kmax(k_a, lo), hi)));
+  c1_out = c1;
+  dmp_out = dmp;
+  return fma(0.5, r2, L.fs[0]);
 }
 
-// March NSTEP consecutive interfaces of one line.  `p` points at v_0 (the
+// March NSTEP consecutive interfaces of one line.  `p` points at F_s (the
 // upwind cell) of the first interface in march order, `ss` is the signed
 // element stride from one interface's upwind cell to the next one's (upwind
 // to downwind), `out` receives the interface values at out[t * ostep].
 template <int NSTEP>
 __device__ __forceinline__ void mp9_march_fp64(const double* __restrict__ p, int ss,
                                                double* __restrict__ out, int ostep) {
-  double v[9], d[8];
+  Mp9Line L;
+  double v[9];
 #pragma unroll
   for (int j = 0; j < 9; ++j) v[j] = p[(j - 4) * ss];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) d[k] = v[k + 1] - v[k];
+  for (int k = 0; k < 8; ++k) L.d[k] = v[k + 1] - v[k];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) L.fs[j] = v[j + 4];
+  L.cm1 = L.d[3] - L.d[2];
+  L.c0 = L.d[4] - L.d[3];
+  L.dmm = minmod4_bits(dbits(fma(4.0, L.c0, -L.cm1)), dbits(fma(4.0, L.cm1, -L.c0)),
+                       dbits(L.c0), dbits(L.cm1));
 #pragma unroll
   for (int t = 0; t < NSTEP; ++t) {
-    out[t * ostep] = mp9_face_fp64(v, d);
+    double c1;
+    long long dmp;
+    out[t * ostep] = mp9_face_fp64(L, c1, dmp);
     if (t + 1 < NSTEP) {
+      const double vnew = p[(t + 5) * ss];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) v[j] = v[j + 1];
-      v[8] = p[(t + 5) * ss];
+      for (int k = 0; k < 7; ++k) L.d[k] = L.d[k + 1];
+      L.d[7] = vnew - L.fs[4];
 #pragma unroll
-      for (int k = 0; k < 7; ++k) d[k] = d[k + 1];
-      d[7] = v[8] - v[7];
+      for (int j = 0; j < 4; ++j) L.fs[j] = L.fs[j + 1];
+      L.fs[4] = vnew;
+      L.cm1 = L.c0;
+      L.c0 = c1;
+      L.dmm = dmp;
     }
   }
 }
