@@ -46,6 +46,8 @@ FLOPS_PER_POP = {"stage3": 48 + 5 + 24, "stage4": 48 + 5 + 14, "final": 48 + 5 +
 # written once each by the kernel (stage 3: F2, F, D -> F3, A4, Af; stage 4:
 # F3, A4, Af -> A4, Af; final: A4, Af -> F, D, F2).
 BYTES_PER_POP = {"stage3": 6 * 8, "stage4": 5 * 8, "final": 5 * 8}
+# Mixed precision: the same arrays in binary32 (4 B per population).
+BYTES_PER_POP_MIXED = {k: v // 2 for k, v in BYTES_PER_POP.items()}
 # binary64 peak: 152 SMs x 2 DFMA lanes/clk/SM (the 1.25 TFLOP/s nominal
 # figure of GB300 at 2070 MHz) x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -255,6 +257,50 @@ def run_ours(args, world, rank, local):
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
     }
 
+    # mixed precision on the same workload and step window: binary32
+    # populations, binary64-accurate moments; error against the binary64 run
+    mixed = None
+    if not args.no_mixed:
+        m = fdlb.Solver.from_workload(wl, precision=fdlb.FDLB_MIXED, stream=stream)
+        m.init_riemann(wl.states, wl.xsplit, wl.ysplit)
+        fdlb.fdlb_step(m.ctx, args.warmup)
+        torch.cuda.synchronize()
+        e0m, e1m = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _barrier(world)
+        e0m.record(stream)
+        mstage = fdlb.fdlb_step_timed(m.ctx, args.steps)
+        e1m.record(stream)
+        torch.cuda.synchronize()
+        mixed_ms = _max_over_ranks(world, e0m.elapsed_time(e1m))
+        mt = max(range(3), key=lambda i: mstage[i])
+        m_launch_ms = mstage[mt] / args.steps
+        m_bytes = BYTES_PER_POP_MIXED[names[mt]] * units_per_step
+        m_gbs = m_bytes / (m_launch_ms * 1e-3) / 1e9
+        # both runs are now at step warmup + steps from the same initial state
+        def fields(sol):
+            n, ux, uy, T = sol.moments()
+            return n, ux, uy, T
+        fn, fu, fv, fT = fields(s)
+        mn, mu, mv, mT = fields(m)
+        relerr = lambda a, b, floor=0.0: float(np.abs(a - b).max() / max(np.abs(b).max(), floor))
+        mixed = {
+            "value": world * units_per_step * args.steps / (mixed_ms * 1e-3), "unit": UNIT,
+            "dtype": "f32 storage/advection, f64-accurate moments",
+            "ms_per_step": mixed_ms / args.steps,
+            "speedup_vs_fp64": elapsed_ms / mixed_ms,
+            "err_vs_fp64": {"n": relerr(mn, fn), "u": relerr(mu, fu, 1.0),
+                            "v": relerr(mv, fv, 1.0), "T": relerr(mT, fT),
+                            "after_steps": args.warmup + args.steps},
+            "roofline": {"bound": "hbm", "kernel": f"stage_kernel<2,8,8,{names[mt]},float>",
+                         "achieved": m_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                         "frac": (m_gbs / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                         "traffic": None, "avg_launch_ms": m_launch_ms,
+                         "stage_ms_per_step": {n: v / args.steps for n, v in zip(names, mstage)}},
+            "gpu_launches": launches_per_step * args.steps,
+        }
+        m.close()
+
     # end to end through the C ABI with host buffers: per step, upload the
     # state from pinned host memory, advance one step, read the moments back.
     host_state = torch.empty(s.shape, dtype=torch.float64, pin_memory=True)
@@ -291,7 +337,7 @@ def run_ours(args, world, rank, local):
                                "gamma=1.4, tau=1e-6, dt=2.5e-5, FP64",
                    "cells": int(N), "populations": int(P), "parallelism": f"replicas{world}",
                    "l2": "working set 1.6 GB > 129 MB L2 (no flush needed)"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
@@ -311,6 +357,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = _dist_setup()

@@ -58,7 +58,7 @@ extern "C" {
 #define FDLB_ETIMEOUT -6    /* reserved: a bounded device wait gave up */
 
 #define FDLB_FP64 0         /* populations stored and computed in binary64 */
-#define FDLB_MIXED 1        /* reserved: binary32 storage and advection, binary64 moments */
+#define FDLB_MIXED 1        /* binary32 storage and advection, binary64-accurate moments */
 
 #define FDLB_BC_OUTLET 0    /* ghosts copy the adjacent fluid node (Sec. IV) */
 #define FDLB_BC_PERIODIC 1  /* periodic images (conservation tests) */
@@ -93,7 +93,12 @@ typedef struct {
  *   tau, dt    : BGK relaxation time (> 0) and time step (> 0);
  *                dt max|p| / dx <= 1 on every axis (Sec. IV CFL condition)
  *   tableau    : NULL for IMEX-SSP3(4,3,3) of Table I
- *   precision  : FDLB_FP64
+ *   precision  : FDLB_FP64: populations stored and computed in binary64;
+ *                FDLB_MIXED: populations stored, advected and relaxed in
+ *                binary32; moment sums formed error-free in binary32 pairs
+ *                and folded into binary64 per cell, so n, u, T (including
+ *                the cancellation in T = (E - n u^2)/((D+K) n)), the
+ *                Hermite factors and the relaxation coefficients are binary64
  *   cuda_stream: cudaStream_t to enqueue on (NULL: the legacy default stream)
  *   out        : receives the context (NULL on failure)
  * The populations start at zero; call fdlb_init_riemann or fdlb_set_state. */

@@ -197,6 +197,13 @@ bool stage_coefficients(const fdlb_tableau& t, double lam, fdlb::StageCoef* sc, 
   return true;
 }
 
+// x = hi + lo with hi = binary32(x) and lo = binary32(x - hi): 48 of x's 53
+// significant bits, for the compensated binary32 moment sums.
+void split_float(double x, float* hi, float* lo) {
+  *hi = (float)x;
+  *lo = (float)(x - (double)*hi);
+}
+
 int ensure_prepared(fdlb_ctx* c) {
   if (c->prepared) return FDLB_OK;
   cudaError_t me = cudaMemsetAsync(c->dp.status, 0, sizeof(unsigned), c->stream);
@@ -282,6 +289,9 @@ int params_for(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double t
     p.py[pop] = ay;
     p.cx[pop] = p.dtdx * ax;
     p.cy[pop] = p.dtdy * ay;
+    split_float(ax, &p.pxh[pop], &p.pxl[pop]);
+    split_float(ay, &p.pyh[pop], &p.pyl[pop]);
+    split_float(p.p2[pop], &p.p2h[pop], &p.p2l[pop]);
   }
   const char* why = nullptr;
   if (!stage_coefficients(tab, dt / tau, &p.sc, &why))
@@ -311,8 +321,9 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
     return set_err(nullptr, FDLB_EINVAL, "empty domain");
   if (g.bc != FDLB_BC_OUTLET && g.bc != FDLB_BC_PERIODIC)
     return set_err(nullptr, FDLB_EINVAL, "bc must be 0 (outlet) or 1 (periodic)");
-  if (precision != FDLB_FP64)
-    return set_err(nullptr, FDLB_EINVAL, "precision %d not available (FDLB_FP64 only)", precision);
+  if (precision != FDLB_FP64 && precision != FDLB_MIXED)
+    return set_err(nullptr, FDLB_EINVAL, "precision must be FDLB_FP64 or FDLB_MIXED (got %d)",
+                   precision);
   if (!fdlb::supported_lattice(g.d, Qphi, Qchi))
     return set_err(nullptr, FDLB_EINVAL, "lattice d=%d Qphi=%d Qchi=%d not compiled", g.d, Qphi,
                    Qchi);
@@ -387,6 +398,9 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
     p.py[pop] = ay;
     p.cx[pop] = p.dtdx * ax;
     p.cy[pop] = p.dtdy * ay;
+    split_float(ax, &p.pxh[pop], &p.pxl[pop]);
+    split_float(ay, &p.pyh[pop], &p.pyl[pop]);
+    split_float(p.p2[pop], &p.p2h[pop], &p.p2l[pop]);
   }
   const char* why = nullptr;
   if (!stage_coefficients(tab, dt / tau, &p.sc, &why)) {
@@ -398,7 +412,9 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
     delete c;
     return cuda_err(nullptr, e, "cudaGetDevice");
   }
-  const size_t arr = (size_t)p.P * (size_t)N * sizeof(double);
+  p.precision = precision;
+  const size_t esize = precision == FDLB_MIXED ? sizeof(float) : sizeof(double);
+  const size_t arr = (size_t)p.P * (size_t)N * esize;
   const size_t mom_bytes = 4 * (size_t)N * sizeof(double);
   c->buf_bytes = 6 * arr + mom_bytes + 256;
   e = cudaMalloc(&c->buf, c->buf_bytes);
@@ -410,12 +426,12 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
                    cudaGetErrorString(e));
   }
   char* b = (char*)c->buf;
-  p.F = (double*)(b + 0 * arr);
-  p.F2 = (double*)(b + 1 * arr);
-  p.F3 = (double*)(b + 2 * arr);
-  p.A4 = (double*)(b + 3 * arr);
-  p.Af = (double*)(b + 4 * arr);
-  p.D = (double*)(b + 5 * arr);
+  p.F = b + 0 * arr;
+  p.F2 = b + 1 * arr;
+  p.F3 = b + 2 * arr;
+  p.A4 = b + 3 * arr;
+  p.Af = b + 4 * arr;
+  p.D = b + 5 * arr;
   c->mom = (double*)(b + 6 * arr);
   p.status = (unsigned*)(b + 6 * arr + mom_bytes);
   e = cudaMallocHost(&c->status_host, sizeof(unsigned));
@@ -537,7 +553,8 @@ int fdlb_moments(fdlb_ctx* c, double* n, double* ux, double* uy, double* T, int 
 
 size_t fdlb_state_bytes(const fdlb_ctx* c) {
   if (!c) return 0;
-  return (size_t)c->dp.P * (size_t)c->dp.N * sizeof(double);
+  const size_t esize = c->precision == FDLB_MIXED ? sizeof(float) : sizeof(double);
+  return (size_t)c->dp.P * (size_t)c->dp.N * esize;
 }
 
 int fdlb_get_state(fdlb_ctx* c, void* dst, int on_device) {

@@ -30,7 +30,7 @@ struct StageCoef {
 };
 
 // Everything a stage kernel needs; passed by value as a __grid_constant__
-// kernel parameter (about 10 KB).
+// kernel parameter (about 14 KB).
 struct DevParams {
   int d, nx, ny, bc;            // dimension, cells, boundary condition
   int Qp, Qc, P, nphi, nchi;    // lattice orders and population counts
@@ -44,12 +44,16 @@ struct DevParams {
   StageCoef sc;
   // per population: dt p_x/dx, dt p_y/dy, p_x, p_y, and p^2 (phi) or 0 (chi)
   double cx[kMaxPop], cy[kMaxPop], px[kMaxPop], py[kMaxPop], p2[kMaxPop];
-  double* F;    // state F^n (and F^{n+1} after the final stage)
-  double* F2;   // stage-2 populations (advected by stage 3)
-  double* F3;   // stage-3 populations (advected by stage 4); pass-1 scratch R3
-  double* A4;   // stage-4 explicit part, then F4 (advected by the final stage)
-  double* Af;   // running explicit part of F^{n+1}
-  double* D;    // F^n - F^n_eq
+  // binary32 splits p = hi + lo of p_x, p_y, p^2 (mixed precision moments)
+  float pxh[kMaxPop], pxl[kMaxPop], pyh[kMaxPop], pyl[kMaxPop], p2h[kMaxPop], p2l[kMaxPop];
+  int precision;  // FDLB_FP64 (double arrays) or FDLB_MIXED (float arrays)
+  // Population arrays, element type double (FDLB_FP64) or float (FDLB_MIXED):
+  void* F;      // state F^n (and F^{n+1} after the final stage)
+  void* F2;     // stage-2 populations (advected by stage 3)
+  void* F3;     // stage-3 populations (advected by stage 4); pass-1 scratch R3
+  void* A4;     // stage-4 explicit part, then F4 (advected by the final stage)
+  void* Af;     // running explicit part of F^{n+1}
+  void* D;      // F^n - F^n_eq
   unsigned* status;  // bit 0: invalid moments seen
 };
 

@@ -151,8 +151,90 @@ __device__ __forceinline__ bool moments_to_nut(const DevParams& p, const Moments
   return (n > 0.0) && (T > 0.0) && isfinite(n) && isfinite(T) && isfinite(ux) && isfinite(uy);
 }
 
+// ---- storage-type helpers --------------------------------------------------
+
+__device__ __forceinline__ double sfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float sfma(float a, float b, float c) { return fmaf(a, b, c); }
+
+// Moment sums of binary32 populations, kept as unevaluated binary32 pairs
+// (hi + lo) with error-free transformations: TwoSum for each addition and the
+// fma-exact product error for p * v with p = hi + lo split on the host.  The
+// pairs carry about 44 significant bits and are folded into binary64 once per
+// cell, so n, u and T = (E - n u^2)/((D+K) n) are recovered at binary64
+// accuracy although the populations are binary32.
+struct MomentsF {
+  float nh, nl, jxh, jxl, jyh, jyl, eh, el;
+};
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+__device__ __forceinline__ void two_prod_acc(float& hi, float& lo, float ph, float pl, float v) {
+  const float prod = __fmul_rn(ph, v);
+  const float perr = fmaf(ph, v, -prod);  // exact: ph * v - prod
+  two_sum_acc(hi, lo, prod);
+  lo = __fadd_rn(lo, fmaf(pl, v, perr));
+}
+
 template <int DIM, int QP, int QC>
-__device__ __forceinline__ double feq_of(const EqCell<DIM, QP, QC>& eq, int pop) {
+__device__ __forceinline__ void accumulate(const DevParams& p, MomentsF& m, int pop, float v) {
+  using L = Lat<DIM, QP, QC>;
+  if (pop < L::NPHI) {
+    two_sum_acc(m.nh, m.nl, v);
+    two_prod_acc(m.jxh, m.jxl, p.pxh[pop], p.pxl[pop], v);
+    if (DIM == 2) two_prod_acc(m.jyh, m.jyl, p.pyh[pop], p.pyl[pop], v);
+    two_prod_acc(m.eh, m.el, p.p2h[pop], p.p2l[pop], v);
+  } else {
+    two_sum_acc(m.eh, m.el, v);
+  }
+}
+
+__device__ __forceinline__ Moments to_fp64(const Moments& m) { return m; }
+__device__ __forceinline__ Moments to_fp64(const MomentsF& m) {
+  return Moments{(double)m.nh + (double)m.nl, (double)m.jxh + (double)m.jxl,
+                 (double)m.jyh + (double)m.jyl, (double)m.eh + (double)m.el};
+}
+
+template <typename S>
+struct MomAcc;
+template <>
+struct MomAcc<double> {
+  using type = Moments;
+};
+template <>
+struct MomAcc<float> {
+  using type = MomentsF;
+};
+
+// Equilibrium factors in the storage type (binary32 copies of the binary64
+// per-cell factors on the mixed path).
+template <int DIM, int QP, int QC, typename S>
+struct EqCellS {
+  S hp[QP], gyp[DIM == 2 ? QP : 1];
+  S hc[QC], gyc[DIM == 2 ? QC : 1];
+};
+
+template <int DIM, int QP, int QC, typename S>
+__device__ __forceinline__ void to_storage(const EqCell<DIM, QP, QC>& a, EqCellS<DIM, QP, QC, S>& b) {
+#pragma unroll
+  for (int k = 0; k < QP; ++k) b.hp[k] = (S)a.hp[k];
+#pragma unroll
+  for (int k = 0; k < QC; ++k) b.hc[k] = (S)a.hc[k];
+  if constexpr (DIM == 2) {
+#pragma unroll
+    for (int k = 0; k < QP; ++k) b.gyp[k] = (S)a.gyp[k];
+#pragma unroll
+    for (int k = 0; k < QC; ++k) b.gyc[k] = (S)a.gyc[k];
+  }
+}
+
+template <int DIM, int QP, int QC, typename S>
+__device__ __forceinline__ S feq_of(const EqCellS<DIM, QP, QC, S>& eq, int pop) {
   using L = Lat<DIM, QP, QC>;
   if (pop < L::NPHI) {
     if constexpr (DIM == 1) return eq.hp[pop];
@@ -163,7 +245,17 @@ __device__ __forceinline__ double feq_of(const EqCell<DIM, QP, QC>& eq, int pop)
   else return eq.hc[q % QC] * eq.gyc[q / QC];
 }
 
-template <int DIM, int QP, int QC, int STAGE>
+// Stage coefficients in the storage type (computed in binary64 on the host).
+template <typename S>
+struct CoefS {
+  S k3, k4, kf, at32, at42, at43, wt2, wt3, wt4, a33e3, a43e3, w3e3, a44e4, w4e4, c2;
+  __device__ __forceinline__ explicit CoefS(const StageCoef& c)
+      : k3((S)c.k3), k4((S)c.k4), kf((S)c.kf), at32((S)c.at32), at42((S)c.at42),
+        at43((S)c.at43), wt2((S)c.wt2), wt3((S)c.wt3), wt4((S)c.wt4), a33e3((S)c.a33e3),
+        a43e3((S)c.a43e3), w3e3((S)c.w3e3), a44e4((S)c.a44e4), w4e4((S)c.w4e4), c2((S)c.c2) {}
+};
+
+template <int DIM, int QP, int QC, int STAGE, typename S>
 __global__ void __launch_bounds__(TileCfg<DIM>::NT)
     stage_kernel(const __grid_constant__ DevParams p) {
   using C = TileCfg<DIM>;
@@ -178,9 +270,15 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
   constexpr int NLINE = DIM == 2 ? TX + TY : 1;
   static_assert(G * NLINE * NSEG == NT, "one march task per thread");
 
-  __shared__ double tile[G][SY][SX];
-  __shared__ double hx[G][TY][TX + 1];
-  __shared__ double hy[DIM == 2 ? G : 1][DIM == 2 ? TX : 1][TY + 1];
+  __shared__ S tile[G][SY][SX];
+  __shared__ S hx[G][TY][TX + 1];
+  __shared__ S hy[DIM == 2 ? G : 1][DIM == 2 ? TX : 1][TY + 1];
+  S* __restrict__ const F = (S*)p.F;
+  S* __restrict__ const F2 = (S*)p.F2;
+  S* __restrict__ const F3 = (S*)p.F3;
+  S* __restrict__ const A4 = (S*)p.A4;
+  S* __restrict__ const Af = (S*)p.Af;
+  S* __restrict__ const Dn = (S*)p.D;
 
   const int tid = threadIdx.x;
   const int x0 = blockIdx.x * TX;
@@ -199,20 +297,20 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
     valid[k] = (c < CELLS) && (x < p.nx) && (y < p.ny);
     cell[k] = (int64_t)y * p.nx + x;
   }
-  Moments mom[CPT];
+  typename MomAcc<S>::type mom[CPT];
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) mom[k] = Moments{0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < CPT; ++k) mom[k] = {};
 
-  const StageCoef& sc = p.sc;
+  const CoefS<S> sc(p.sc);
 
   if (STAGE == kPrep) {
     for (int pop = 0; pop < L::P; ++pop) {
 #pragma unroll
       for (int k = 0; k < CPT; ++k)
-        if (valid[k]) accumulate<DIM, QP, QC>(p, mom[k], pop, p.F[pop * N + cell[k]]);
+        if (valid[k]) accumulate<DIM, QP, QC>(p, mom[k], pop, F[pop * N + cell[k]]);
     }
   } else {
-    const double* __restrict__ adv = (STAGE == kStage3) ? p.F2 : (STAGE == kStage4) ? p.F3 : p.A4;
+    const S* __restrict__ adv = (STAGE == kStage3) ? F2 : (STAGE == kStage4) ? F3 : A4;
     // this thread's march task: population tg of the group, line, segment
     const int tg = tid / (NLINE * NSEG);
     const int tline = (tid / NSEG) % NLINE;
@@ -224,7 +322,7 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
         const int r = (i / SX) % SY;
         const int cidx = i % SX;
         const int pop = g0 + g;
-        double v = 0.0;
+        S v = 0;
         if (pop < L::P && cidx < TX + 2 * H) {
           const int gx = wrap_or_clamp(x0 - H + cidx, p.nx, p.bc);
           const int gy = (DIM == 2) ? wrap_or_clamp(y0 - H + r, p.ny, p.bc) : 0;
@@ -249,10 +347,10 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
         // is (base, element stride) in the tile and its output row
         const int r = (DIM == 2 && xline) ? tline : 0;  // x line: tile row
         const int c = xline ? 0 : tline - TY;           // y line: tile column
-        const double* base = xline ? &tile[tg][r + (DIM == 2 ? H : 0)][up] : &tile[tg][up][c + H];
+        const S* base = xline ? &tile[tg][r + (DIM == 2 ? H : 0)][up] : &tile[tg][up][c + H];
         const int stride = xline ? 1 : SX;
-        double* out = xline ? &hx[tg][r][first] : &hy[tg][c][first];
-        mp9_march_fp64<SEG>(base, sgn * stride, out, sgn);
+        S* out = xline ? &hx[tg][r][first] : &hy[tg][c][first];
+        mp9_march<SEG>(base, sgn * stride, out, sgn);
       }
       __syncthreads();
       // ---- flux difference, explicit part, moments (pass 1)
@@ -265,23 +363,23 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
           const int pop = g0 + g;
           if (pop >= L::P) break;
           // X = dt * (p . grad F) = dt p_x (Fhat_{x+1/2} - Fhat_{x-1/2})/dx + (y)
-          double X = p.cx[pop] * (hx[g][ly][lx + 1] - hx[g][ly][lx]);
-          if constexpr (DIM == 2) X = fma(p.cy[pop], hy[g][lx][ly + 1] - hy[g][lx][ly], X);
+          S X = (S)p.cx[pop] * (hx[g][ly][lx + 1] - hx[g][ly][lx]);
+          if constexpr (DIM == 2) X = sfma((S)p.cy[pop], hy[g][lx][ly + 1] - hy[g][lx][ly], X);
           const int64_t e = pop * N + cell[k];
-          double R;
+          S R;
           if (STAGE == kStage3) {
-            const double f = p.F[e], dd = p.D[e];
-            R = fma(-sc.at32, X, fma(-sc.k3, dd, f));
-            p.F3[e] = R;
-            p.A4[e] = fma(-sc.at42, X, fma(-sc.k4, dd, f));
-            p.Af[e] = fma(-sc.wt2, X, fma(-sc.kf, dd, f));
+            const S f = F[e], dd = Dn[e];
+            R = sfma(-sc.at32, X, sfma(-sc.k3, dd, f));
+            F3[e] = R;
+            A4[e] = sfma(-sc.at42, X, sfma(-sc.k4, dd, f));
+            Af[e] = sfma(-sc.wt2, X, sfma(-sc.kf, dd, f));
           } else if (STAGE == kStage4) {
-            R = fma(-sc.at43, X, p.A4[e]);
-            p.A4[e] = R;
-            p.Af[e] = fma(-sc.wt3, X, p.Af[e]);
+            R = sfma(-sc.at43, X, A4[e]);
+            A4[e] = R;
+            Af[e] = sfma(-sc.wt3, X, Af[e]);
           } else {  // kFinal: F^{n+1}
-            R = fma(-sc.wt4, X, p.Af[e]);
-            p.F[e] = R;
+            R = sfma(-sc.wt4, X, Af[e]);
+            F[e] = R;
           }
           accumulate<DIM, QP, QC>(p, mom[k], pop, R);
         }
@@ -295,30 +393,32 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
   for (int k = 0; k < CPT; ++k) {
     if (!valid[k]) continue;
     double n, ux, uy, T;
-    if (!moments_to_nut<DIM>(p, mom[k], n, ux, uy, T)) atomicOr(p.status, 1u);
-    EqCell<DIM, QP, QC> eq;
-    make_eq_nut<DIM, QP, QC>(p, n, ux, uy, T, eq);
+    if (!moments_to_nut<DIM>(p, to_fp64(mom[k]), n, ux, uy, T)) atomicOr(p.status, 1u);
+    EqCell<DIM, QP, QC> eq64;
+    make_eq_nut<DIM, QP, QC>(p, n, ux, uy, T, eq64);
+    EqCellS<DIM, QP, QC, S> eq;
+    to_storage(eq64, eq);
     const int64_t c = cell[k];
 #pragma unroll
     for (int pop = 0; pop < L::P; ++pop) {
       const int64_t e = pop * N + c;
-      const double fe = feq_of<DIM, QP, QC>(eq, pop);
+      const S fe = feq_of<DIM, QP, QC, S>(eq, pop);
       if (STAGE == kStage3) {
-        const double R = p.F3[e];
-        const double D3 = R - fe;
-        p.F3[e] = fma(-sc.a33e3, D3, R);
-        p.A4[e] = fma(-sc.a43e3, D3, p.A4[e]);
-        p.Af[e] = fma(-sc.w3e3, D3, p.Af[e]);
+        const S R = F3[e];
+        const S D3 = R - fe;
+        F3[e] = sfma(-sc.a33e3, D3, R);
+        A4[e] = sfma(-sc.a43e3, D3, A4[e]);
+        Af[e] = sfma(-sc.w3e3, D3, Af[e]);
       } else if (STAGE == kStage4) {
-        const double R = p.A4[e];
-        const double D4 = R - fe;
-        p.A4[e] = fma(-sc.a44e4, D4, R);
-        p.Af[e] = fma(-sc.w4e4, D4, p.Af[e]);
+        const S R = A4[e];
+        const S D4 = R - fe;
+        A4[e] = sfma(-sc.a44e4, D4, R);
+        Af[e] = sfma(-sc.w4e4, D4, Af[e]);
       } else {  // kPrep / kFinal: D and F2 of the new state
-        const double f = p.F[e];
-        const double dd = f - fe;
-        p.D[e] = dd;
-        p.F2[e] = fma(sc.c2, dd, fe);
+        const S f = F[e];
+        const S dd = f - fe;
+        Dn[e] = dd;
+        F2[e] = sfma(sc.c2, dd, fe);
       }
     }
   }
@@ -331,7 +431,7 @@ struct RiemannArgs {
   double xsplit, ysplit, x0, dx, y0, dy;
 };
 
-template <int DIM, int QP, int QC>
+template <int DIM, int QP, int QC, typename S>
 __global__ void init_riemann_kernel(const __grid_constant__ DevParams p,
                                     const __grid_constant__ RiemannArgs a) {
   using L = Lat<DIM, QP, QC>;
@@ -350,47 +450,58 @@ __global__ void init_riemann_kernel(const __grid_constant__ DevParams p,
   const double ux = a.st[q][1];
   const double uy = DIM == 2 ? a.st[q][2] : 0.0;
   const double P = a.st[q][DIM == 2 ? 3 : 2];
-  EqCell<DIM, QP, QC> eq;
-  make_eq_nut<DIM, QP, QC>(p, rho, ux, uy, P / rho, eq);
+  EqCell<DIM, QP, QC> eq64;
+  make_eq_nut<DIM, QP, QC>(p, rho, ux, uy, P / rho, eq64);
+  EqCellS<DIM, QP, QC, double> eq;  // binary64 products, rounded once on store
+  to_storage(eq64, eq);
+  S* F = (S*)p.F;
 #pragma unroll
-  for (int pop = 0; pop < L::P; ++pop) p.F[pop * p.N + c] = feq_of<DIM, QP, QC>(eq, pop);
+  for (int pop = 0; pop < L::P; ++pop) F[pop * p.N + c] = (S)feq_of<DIM, QP, QC, double>(eq, pop);
 }
 
-template <int DIM, int QP, int QC>
+template <int DIM, int QP, int QC, typename S>
 __global__ void moments_kernel(const __grid_constant__ DevParams p, double* __restrict__ n,
                                double* __restrict__ ux, double* __restrict__ uy,
                                double* __restrict__ T) {
   using L = Lat<DIM, QP, QC>;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.N) return;
-  Moments m{0.0, 0.0, 0.0, 0.0};
-  for (int pop = 0; pop < L::P; ++pop) accumulate<DIM, QP, QC>(p, m, pop, p.F[pop * p.N + c]);
+  typename MomAcc<S>::type m = {};
+  const S* F = (const S*)p.F;
+  for (int pop = 0; pop < L::P; ++pop) accumulate<DIM, QP, QC>(p, m, pop, F[pop * p.N + c]);
   double nn, vx, vy, TT;
-  moments_to_nut<DIM>(p, m, nn, vx, vy, TT);
+  moments_to_nut<DIM>(p, to_fp64(m), nn, vx, vy, TT);
   n[c] = nn;
   ux[c] = vx;
   if (DIM == 2 && uy) uy[c] = vy;
   T[c] = TT;
 }
 
-template <int DIM, int QP, int QC>
-int launch_stage_t(const DevParams& p, int stage, cudaStream_t s) {
+template <int DIM, int QP, int QC, typename S>
+int launch_stage_ts(const DevParams& p, int stage, cudaStream_t s) {
   using C = TileCfg<DIM>;
   dim3 grid((p.nx + C::TX - 1) / C::TX, DIM == 2 ? (p.ny + C::TY - 1) / C::TY : 1);
   switch (stage) {
-    case kPrep: stage_kernel<DIM, QP, QC, kPrep><<<grid, C::NT, 0, s>>>(p); break;
-    case kStage3: stage_kernel<DIM, QP, QC, kStage3><<<grid, C::NT, 0, s>>>(p); break;
-    case kStage4: stage_kernel<DIM, QP, QC, kStage4><<<grid, C::NT, 0, s>>>(p); break;
-    default: stage_kernel<DIM, QP, QC, kFinal><<<grid, C::NT, 0, s>>>(p); break;
+    case kPrep: stage_kernel<DIM, QP, QC, kPrep, S><<<grid, C::NT, 0, s>>>(p); break;
+    case kStage3: stage_kernel<DIM, QP, QC, kStage3, S><<<grid, C::NT, 0, s>>>(p); break;
+    case kStage4: stage_kernel<DIM, QP, QC, kStage4, S><<<grid, C::NT, 0, s>>>(p); break;
+    default: stage_kernel<DIM, QP, QC, kFinal, S><<<grid, C::NT, 0, s>>>(p); break;
   }
   return (int)cudaGetLastError();
+}
+
+template <int DIM, int QP, int QC>
+int launch_stage_t(const DevParams& p, int stage, cudaStream_t s) {
+  return p.precision == 1 ? launch_stage_ts<DIM, QP, QC, float>(p, stage, s)
+                          : launch_stage_ts<DIM, QP, QC, double>(p, stage, s);
 }
 
 template <int DIM, int QP, int QC>
 int launch_init_t(const DevParams& p, const RiemannArgs& a, cudaStream_t s) {
   const int nt = 128;
   const int64_t nb = (p.N + nt - 1) / nt;
-  init_riemann_kernel<DIM, QP, QC><<<(unsigned)nb, nt, 0, s>>>(p, a);
+  if (p.precision == 1) init_riemann_kernel<DIM, QP, QC, float><<<(unsigned)nb, nt, 0, s>>>(p, a);
+  else init_riemann_kernel<DIM, QP, QC, double><<<(unsigned)nb, nt, 0, s>>>(p, a);
   return (int)cudaGetLastError();
 }
 
@@ -399,7 +510,8 @@ int launch_moments_t(const DevParams& p, double* n, double* ux, double* uy, doub
                      cudaStream_t s) {
   const int nt = 128;
   const int64_t nb = (p.N + nt - 1) / nt;
-  moments_kernel<DIM, QP, QC><<<(unsigned)nb, nt, 0, s>>>(p, n, ux, uy, T);
+  if (p.precision == 1) moments_kernel<DIM, QP, QC, float><<<(unsigned)nb, nt, 0, s>>>(p, n, ux, uy, T);
+  else moments_kernel<DIM, QP, QC, double><<<(unsigned)nb, nt, 0, s>>>(p, n, ux, uy, T);
   return (int)cudaGetLastError();
 }
 

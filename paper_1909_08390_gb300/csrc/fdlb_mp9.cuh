@@ -165,3 +165,87 @@ __device__ __forceinline__ void mp9_march_fp64(const double* __restrict__ p, int
 }
 
 }  // namespace fdlb
+
+namespace fdlb {
+
+// binary32 version for the mixed-precision path: the same offset-form
+// formulas on the binary32 pipe, with native min/max (cheap in binary32).
+struct Mp9LineF {
+  float fs[5];
+  float d[8];
+  float cm1, c0, dmm;
+};
+
+__device__ __forceinline__ float minmod4f(float a, float b, float c, float d) {
+  const float lo = fminf(fminf(a, b), fminf(c, d));
+  const float hi = fmaxf(fmaxf(a, b), fmaxf(c, d));
+  return lo > 0.0f ? lo : (hi < 0.0f ? hi : 0.0f);
+}
+
+__device__ __forceinline__ float mp9_face_fp32(const Mp9LineF& L, float& c1_out, float& dmp_out) {
+  const float* d = L.d;
+  float a = (-4.0f / 2520.0f) * d[0];
+  a = fmaf(37.0f / 2520.0f, d[1], a);
+  a = fmaf(-162.0f / 2520.0f, d[2], a);
+  a = fmaf(479.0f / 2520.0f, d[3], a);
+  a = fmaf(1120.0f / 2520.0f, d[4], a);
+  a = fmaf(-255.0f / 2520.0f, d[5], a);
+  a = fmaf(50.0f / 2520.0f, d[6], a);
+  a = fmaf(-5.0f / 2520.0f, d[7], a);
+  const float c1 = d[5] - d[4];
+  const float c0 = L.c0;
+  const float dmp = minmod4f(fmaf(4.0f, c0, -c1), fmaf(4.0f, c1, -c0), c0, c1);
+  const float md = 0.5f * (d[4] - dmp);
+  const float ul = 4.0f * d[3];
+  const float lc = fmaf(4.0f / 3.0f, L.dmm, 0.5f * d[3]);
+  const float lo = fmaxf(fminf(0.0f, fminf(d[4], md)), fminf(0.0f, fminf(ul, lc)));
+  const float hi = fminf(fmaxf(0.0f, fmaxf(d[4], md)), fmaxf(0.0f, fmaxf(ul, lc)));
+  c1_out = c1;
+  dmp_out = dmp;
+  return L.fs[0] + fminf(fmaxf(a, lo), hi);
+}
+
+template <int NSTEP>
+__device__ __forceinline__ void mp9_march_fp32(const float* __restrict__ p, int ss,
+                                               float* __restrict__ out, int ostep) {
+  Mp9LineF L;
+  float v[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) v[j] = p[(j - 4) * ss];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) L.d[k] = v[k + 1] - v[k];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) L.fs[j] = v[j + 4];
+  L.cm1 = L.d[3] - L.d[2];
+  L.c0 = L.d[4] - L.d[3];
+  L.dmm = minmod4f(fmaf(4.0f, L.c0, -L.cm1), fmaf(4.0f, L.cm1, -L.c0), L.c0, L.cm1);
+#pragma unroll
+  for (int t = 0; t < NSTEP; ++t) {
+    float c1, dmp;
+    out[t * ostep] = mp9_face_fp32(L, c1, dmp);
+    if (t + 1 < NSTEP) {
+      const float vnew = p[(t + 5) * ss];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) L.d[k] = L.d[k + 1];
+      L.d[7] = vnew - L.fs[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) L.fs[j] = L.fs[j + 1];
+      L.fs[4] = vnew;
+      L.cm1 = L.c0;
+      L.c0 = c1;
+      L.dmm = dmp;
+    }
+  }
+}
+
+// Overloads so the stage kernel can march either storage type.
+template <int NSTEP>
+__device__ __forceinline__ void mp9_march(const double* p, int ss, double* out, int ostep) {
+  mp9_march_fp64<NSTEP>(p, ss, out, ostep);
+}
+template <int NSTEP>
+__device__ __forceinline__ void mp9_march(const float* p, int ss, float* out, int ostep) {
+  mp9_march_fp32<NSTEP>(p, ss, out, ostep);
+}
+
+}  // namespace fdlb

@@ -246,6 +246,8 @@ class Solver:
         self.ctx = fdlb_create(g, Qphi, Qchi, gamma, tau, dt, tableau, precision, stream)
         self.P = fdlb_npop(self.ctx)
         self.N = fdlb_ncells(self.ctx)
+        self.precision = precision
+        self.dtype = np.float32 if precision == FDLB_MIXED else np.float64
 
     @classmethod
     def from_workload(cls, wl, precision: int = FDLB_FP64, stream=None, **kw):
@@ -265,15 +267,17 @@ class Solver:
         fdlb_step(self.ctx, nsteps)
 
     def state(self) -> np.ndarray:
-        out = np.empty(self.shape, dtype=np.float64)
+        """The populations, float64 (FDLB_FP64) or float32 (FDLB_MIXED)."""
+        out = np.empty(self.shape, dtype=self.dtype)
         fdlb_get_state(self.ctx, out, False)
         return out
 
     def set_state(self, F):
         if hasattr(F, "data_ptr"):
+            assert F.element_size() == np.dtype(self.dtype).itemsize
             fdlb_set_state(self.ctx, F, True)
         else:
-            F = np.ascontiguousarray(F, dtype=np.float64)
+            F = np.ascontiguousarray(F, dtype=self.dtype)
             assert F.size == self.P * self.N
             fdlb_set_state(self.ctx, F, False)
 

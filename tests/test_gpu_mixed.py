@@ -1,0 +1,104 @@
+"""Mixed precision (binary32 populations, binary64-accurate moments,
+temperature and relaxation coefficients) against the binary64 CPU oracle and
+the binary64 GPU path, through the C ABI.
+
+Bar: 1e-5 relative (||.||_inf / ||.||_inf) in n, u (normalised by
+max(|u|, 1)) and T, and in the populations.  Storage rounds every population
+to 24 bits (6e-8 relative) at each of the four stages; the MP-9/limiter
+arithmetic and the relaxation run in binary32; the moments are summed with
+error-free binary32 transformations and folded into binary64, so the
+cancellation in T = (E - n u^2)/((D+K) n) is not amplified.
+"""
+import numpy as np
+import pytest
+
+from paper_1909_08390_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1909_08390_gb300 import build as B, fdlb
+    B.build()
+    fdlb.load()
+    return fdlb
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def fields_err(got, want):
+    n, ux, uy, T = got
+    on, oux, ouy, oT = want
+    e = {"n": rel(n, on), "T": rel(T, oT),
+         "u": np.abs(ux - oux).max() / max(np.abs(oux).max(), 1.0)}
+    if uy is not None:
+        e["v"] = np.abs(uy - ouy).max() / max(np.abs(ouy).max(), 1.0)
+    return e
+
+
+def test_mixed_sod_1d_against_oracle(oracle, F):
+    """1-D Sod (Nx = 400, Q = 8, gamma = 7/5, tau = 1e-6, dt = 5e-5) to
+    t = 0.1, 2000 steps."""
+    wl = W.sod_1d()
+    pr = oracle.Problem(d=1, nx=wl.nx, x0=wl.x0, x1=wl.x1, Qphi=8, Qchi=8, gamma=wl.gamma,
+                        tau=wl.tau, dt=wl.dt)
+    want = oracle.step(pr, oracle.init_states(pr, wl.states, wl.xsplit), wl.nsteps)
+    with F.Solver.from_workload(wl, precision=F.FDLB_MIXED) as s:
+        s.init_riemann(wl.states, wl.xsplit)
+        s.step(wl.nsteps)
+        G = s.state()
+        assert G.dtype == np.float32
+        err = fields_err(s.moments(), oracle.moments(pr, want))
+        assert max(err.values()) < TOL, err
+        assert rel(G.astype(np.float64), want) < TOL
+
+
+@pytest.mark.parametrize("Q", [(8, 8), (5, 3)])
+@pytest.mark.parametrize("shape", [(37, 29), (16, 16), (5, 3)])
+def test_mixed_2d_quadrants_against_oracle(oracle, F, Q, shape):
+    nx, ny = shape
+    wl = W.quadrant_2d(W.BENCH_SEED)
+    pr = oracle.Problem(d=2, nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, Qphi=Q[0], Qchi=Q[1],
+                        gamma=1.4, tau=1e-6, dt=2.5e-5 * 512 / max(nx, ny, 16) / 4)
+    want = oracle.step(pr, oracle.init_states(pr, wl.states, 0.5, 0.5), 40)
+    with F.Solver(d=2, nx=nx, ny=ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, Qphi=Q[0], Qchi=Q[1],
+                  gamma=1.4, tau=1e-6, dt=pr.dt, precision=F.FDLB_MIXED) as s:
+        s.init_riemann(wl.states, 0.5, 0.5)
+        s.step(40)
+        err = fields_err(s.moments(), oracle.moments(pr, want))
+        assert max(err.values()) < TOL, err
+
+
+def test_mixed_512_against_fp64_gpu(F):
+    """The benchmark workload (512 x 512, 128 populations): mixed and binary64
+    GPU runs agree to 1e-5 in n, u, v, T after 50 steps."""
+    wl = W.quadrant_2d(W.BENCH_SEED)
+    out = {}
+    for prec in (F.FDLB_FP64, F.FDLB_MIXED):
+        with F.Solver.from_workload(wl, precision=prec) as s:
+            s.init_riemann(wl.states, 0.5, 0.5)
+            s.step(50)
+            out[prec] = s.moments()
+    err = fields_err(out[F.FDLB_MIXED], out[F.FDLB_FP64])
+    assert max(err.values()) < TOL, err
+
+
+def test_mixed_conservation_periodic(F):
+    """Periodic 2-D box: the binary64-accurate moment sums keep mass,
+    momentum and energy to binary32 storage precision over 200 steps."""
+    shape = (64, 40)
+    with F.Solver(d=2, nx=shape[0], ny=shape[1], x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=1, Qphi=8,
+                  Qchi=8, gamma=1.4, tau=1e-5, dt=5e-4, precision=F.FDLB_MIXED) as s:
+        F0 = W.smooth_random_populations(s.shape, seed=5, amp=0.2).astype(np.float32)
+        s.set_state(F0)
+        n0, ux0, uy0, T0 = s.moments()
+        s.step(200)
+        n1, ux1, uy1, T1 = s.moments()
+    tot = lambda n, ux, uy, T: np.array([n.sum(), (n * ux).sum(), (n * uy).sum(),
+                                         (n * (ux * ux + uy * uy) + 5.0 * n * T).sum()])
+    a, b = tot(n0, ux0, uy0, T0), tot(n1, ux1, uy1, T1)
+    assert np.all(np.abs(a - b) <= 1e-5 * np.maximum(np.abs(a), 1.0)), (a, b)
