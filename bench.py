@@ -48,6 +48,34 @@ FLOPS_PER_POP = {"stage3": 48 + 5 + 24, "stage4": 48 + 5 + 14, "final": 48 + 5 +
 BYTES_PER_POP = {"stage3": 6 * 8, "stage4": 5 * 8, "final": 5 * 8}
 # Mixed precision: the same arrays in binary32 (4 B per population).
 BYTES_PER_POP_MIXED = {k: v // 2 for k, v in BYTES_PER_POP.items()}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu captures summarised in profiles/stage_kernel_fp64_quadrant512.md and
+# profiles/stage_kernel_mixed_quadrant512.md, valid for the kernel sources
+# whose SHA-256 (over paper_1909_08390_gb300/csrc/*, sorted) is recorded here;
+# reported as null once the sources differ.
+TRAFFIC_SRC_SHA256 = "75abe7901dac9d556c96990c6b918cdafafe18ade0567929e3e6927184f5b5bc"
+TRAFFIC_BYTES = {
+    "fp64": {"stage3": 3168712000, "stage4": 2338937000, "final": 1558368000},
+    "mixed": {"stage3": 1563743232, "stage4": 1155023616, "final": 757150720},
+}
+
+
+def _kernel_sources_sha256():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for path in sorted(glob.glob(os.path.join(ROOT, "paper_1909_08390_gb300", "csrc", "*"))):
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _traffic(kind, stage):
+    if _kernel_sources_sha256() != TRAFFIC_SRC_SHA256:
+        return None
+    return TRAFFIC_BYTES[kind][stage]
+
+
 # binary64 peak: 152 SMs x 2 DFMA lanes/clk/SM (the 1.25 TFLOP/s nominal
 # figure of GB300 at 2070 MHz) x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -249,7 +277,7 @@ def run_ours(args, world, rank, local):
         "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved_tflops / FP64_PEAK_TFLOPS,
         "peak_source": "binary64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
-        "traffic": None,
+        "traffic": _traffic("fp64", names[top]),
         "algorithmic_flops_per_launch": flops,
         "avg_launch_ms": per_launch_ms,
         "stage_ms_per_step": {n: v / args.steps for n, v in zip(names, stage_ms)},
@@ -295,7 +323,7 @@ def run_ours(args, world, rank, local):
                          "achieved": m_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": (m_gbs / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                         "traffic": None, "avg_launch_ms": m_launch_ms,
+                         "traffic": _traffic("mixed", names[mt]), "avg_launch_ms": m_launch_ms,
                          "stage_ms_per_step": {n: v / args.steps for n, v in zip(names, mstage)}},
             "gpu_launches": launches_per_step * args.steps,
         }
