@@ -148,6 +148,48 @@ int fdlb_set_stream(fdlb_ctx* ctx, void* cuda_stream);
 /* Number of kernel launches fdlb_step makes per step (for launch accounting). */
 int fdlb_launches_per_step(const fdlb_ctx* ctx);
 
+/* ---- batches of independent 1-D problems ------------------------------------
+ * One context holds nprob two-state problems of their own length and gamma
+ * on the same domain [x0, x1], lattice, tau and dt.  Their cells are
+ * concatenated: problem i owns cells [base_i, base_i + nx[i]) of the state
+ * F[P][ncells], base_0 = 0, base_{i+1} = base_i + nx[i]; ghosts (Sec. IV)
+ * copy each problem's own end cells.  Every stage runs all problems in one
+ * launch of a persistent grid walking a work list of tiles, and fdlb_step
+ * replays the steps from a captured CUDA graph.  fdlb_step, fdlb_step_timed,
+ * fdlb_moments (n, u, T per concatenated cell), fdlb_get_state,
+ * fdlb_set_state and fdlb_destroy work on batch contexts; fdlb_init_riemann
+ * does not (use fdlb_batch_init_riemann).
+ *   nx[nprob], gamma[nprob]: host arrays; nx >= 1, D+K-1 >= 0, CFL <= 1 each
+ *   Qphi, Qchi: (8, 8) or (5, 3); precision: FDLB_FP64 or FDLB_MIXED */
+int fdlb_create_batch(int nprob, const int64_t* nx, const double* gamma, double x0, double x1,
+                      int Qphi, int Qchi, double tau, double dt, int precision, void* cuda_stream,
+                      fdlb_ctx** out);
+
+/* Equilibrium Riemann data of every problem of a batch: states is a host
+ * array [nprob][2][3] of (rho, u, P) left and right, xsplit[nprob] the
+ * membranes (NULL: the domain centres).  rho, P > 0. */
+int fdlb_batch_init_riemann(fdlb_ctx* ctx, const double* states, const double* xsplit);
+
+/* flags[nprob] (host): bit 0 set for each problem in which a cell reached
+ * n <= 0, T <= 0 or a non-finite moment since the last initialisation.  The
+ * problems do not interact, so the other members stay valid; fdlb_step
+ * returns FDLB_EUNSTABLE as soon as any member is flagged. */
+int fdlb_batch_status(fdlb_ctx* ctx, unsigned* flags);
+
+/* base[nprob]: the first concatenated cell of each problem. */
+int fdlb_batch_offsets(const fdlb_ctx* ctx, int64_t* base);
+
+/* Autotuner of a batch context: times trial_steps steps of every tile shape
+ * (cells per tile 127, 63, 255) and persistent-grid size (2, 4, 8, 16 CTAs
+ * per SM) on the context's own problems, starting each trial from the
+ * current state, restores the state and keeps the fastest shape.  The
+ * chosen shape is returned in *variant_out and *ctas_per_sm_out (either may
+ * be NULL).  Allocates one temporary state copy. */
+int fdlb_autotune(fdlb_ctx* ctx, int trial_steps, int* variant_out, int* ctas_per_sm_out);
+
+/* Set the batch tile shape directly (variant 0, 1, 2 = 127, 63, 255 cells). */
+int fdlb_batch_set_tiling(fdlb_ctx* ctx, int variant, int ctas_per_sm);
+
 /* The Gauss-Hermite rule of order Q (1 <= Q <= 16) the library uses for
  * weight exp(-p^2/2)/sqrt(2 pi): p[0..Q-1] the roots of He_Q in ascending
  * order, w[0..Q-1] = Q!/He_{Q+1}(p_k)^2 (Sec. II).  Host arrays; no GPU

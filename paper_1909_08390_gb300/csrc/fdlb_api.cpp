@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+
 #include "fdlb.h"
 #include "fdlb_internal.h"
 
@@ -29,6 +31,15 @@ struct fdlb_ctx {
   unsigned* status_host = nullptr;  // pinned
   bool prepared = false;
   std::string err;
+  // batches of 1-D problems (fdlb_create_batch)
+  bool batch = false;
+  std::vector<fdlb::BatchProblem> probs;
+  fdlb::BatchProblem* probs_dev = nullptr;
+  fdlb::WorkItem* work_dev = nullptr;
+  int nsm = 0;
+  // CUDA graph of kGraphSteps steps, captured on first use
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
 };
 
 namespace {
@@ -204,11 +215,55 @@ void split_float(double x, float* hi, float* lo) {
   *lo = (float)(x - (double)*hi);
 }
 
+// One stage of a context: the grid-mapped kernels of a single problem or the
+// persistent work-list kernels of a batch.
+int launch_stage_any(const fdlb_ctx* c, int stage, cudaStream_t s) {
+  return c->batch ? fdlb::launch_batch_stage(c->dp, stage, s) : fdlb::launch_stage(c->dp, stage, s);
+}
+
+constexpr int kGraphSteps = 16;  // steps per captured graph
+
+void drop_graph(fdlb_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+}
+
+// Capture kGraphSteps steps (3 kernels each) on a private stream once; the
+// graph then replays on the context's stream.
+int ensure_graph(fdlb_ctx* c) {
+  if (c->graph_exec) return FDLB_OK;
+  cudaError_t e = cudaSuccess;
+  if (!c->capture_stream) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_err(c, e, "capture stream");
+  e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_err(c, e, "cudaStreamBeginCapture");
+  int le = 0;
+  for (int k = 0; k < kGraphSteps && !le; ++k)
+    for (int st : {fdlb::kStage3, fdlb::kStage4, fdlb::kFinal})
+      if (!le) le = launch_stage_any(c, st, c->capture_stream);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->capture_stream, &g);
+  if (le) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_err(c, (cudaError_t)le, "kernel launch during capture");
+  }
+  if (e != cudaSuccess) return cuda_err(c, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph_exec = nullptr;
+    return cuda_err(c, e, "cudaGraphInstantiate");
+  }
+  return FDLB_OK;
+}
+
 int ensure_prepared(fdlb_ctx* c) {
   if (c->prepared) return FDLB_OK;
   cudaError_t me = cudaMemsetAsync(c->dp.status, 0, sizeof(unsigned), c->stream);
+  if (me == cudaSuccess && c->batch)
+    me = cudaMemsetAsync(c->dp.pstatus, 0, c->probs.size() * sizeof(unsigned), c->stream);
   if (me != cudaSuccess) return cuda_err(c, me, "status reset");
-  int e = fdlb::launch_stage(c->dp, fdlb::kPrep, c->stream);
+  int e = launch_stage_any(c, fdlb::kPrep, c->stream);
   if (e) return cuda_err(c, (cudaError_t)e, "prepare kernel launch");
   c->prepared = true;
   return FDLB_OK;
@@ -448,6 +503,7 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
 
 int fdlb_init_riemann(fdlb_ctx* c, const double* states, int nq, double xsplit, double ysplit) {
   if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
+  if (c->batch) return set_err(c, FDLB_EINVAL, "batch context: use fdlb_batch_init_riemann");
   if (!states) return set_err(c, FDLB_EINVAL, "states is NULL");
   const int d = c->dp.d;
   if ((d == 1 && nq != 2) || (d == 2 && nq != 4))
@@ -474,9 +530,18 @@ int fdlb_step(fdlb_ctx* c, int64_t nsteps) {
   if (nsteps < 0) return set_err(c, FDLB_EINVAL, "nsteps < 0");
   int rc = ensure_prepared(c);
   if (rc) return rc;
-  for (int64_t s = 0; s < nsteps; ++s) {
+  int64_t left = nsteps;
+  if (nsteps >= kGraphSteps) {
+    rc = ensure_graph(c);
+    if (rc) return rc;
+    for (; left >= kGraphSteps; left -= kGraphSteps) {
+      cudaError_t ge = cudaGraphLaunch(c->graph_exec, c->stream);
+      if (ge != cudaSuccess) return cuda_err(c, ge, "cudaGraphLaunch");
+    }
+  }
+  for (int64_t s = 0; s < left; ++s) {
     for (int st : {fdlb::kStage3, fdlb::kStage4, fdlb::kFinal}) {
-      int e = fdlb::launch_stage(c->dp, st, c->stream);
+      int e = launch_stage_any(c, st, c->stream);
       if (e) return cuda_err(c, (cudaError_t)e, "stage kernel launch");
     }
   }
@@ -503,7 +568,7 @@ int fdlb_step_timed(fdlb_ctx* c, int64_t nsteps, double* stage_ms) {
   if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
   for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s) {
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-      int le = fdlb::launch_stage(c->dp, kinds[k], c->stream);
+      int le = launch_stage_any(c, kinds[k], c->stream);
       if (le) e = (cudaError_t)le;
       if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + k + 1], c->stream);
     }
@@ -586,6 +651,253 @@ int fdlb_set_state(fdlb_ctx* c, const void* src, int on_device) {
   return FDLB_OK;
 }
 
+// ---- batches of 1-D problems -------------------------------------------------
+
+namespace {
+
+int upload_work(fdlb_ctx* c) {
+  const int tx = fdlb::batch_tile_cells(c->dp.variant);
+  std::vector<fdlb::WorkItem> work;
+  for (int i = 0; i < (int)c->probs.size(); ++i)
+    for (int x = 0; x < c->probs[i].nx; x += tx) work.push_back(fdlb::WorkItem{i, x});
+  if (c->work_dev) cudaFree(c->work_dev);
+  c->work_dev = nullptr;
+  cudaError_t e = cudaMalloc(&c->work_dev, work.size() * sizeof(fdlb::WorkItem));
+  if (e != cudaSuccess) return set_err(c, FDLB_ENOMEM, "work list: %s", cudaGetErrorString(e));
+  e = cudaMemcpyAsync(c->work_dev, work.data(), work.size() * sizeof(fdlb::WorkItem),
+                      cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "work list upload");
+  c->dp.work = c->work_dev;
+  c->dp.nwork = (int)work.size();
+  return FDLB_OK;
+}
+
+int upload_probs(fdlb_ctx* c) {
+  cudaError_t e = cudaMemcpyAsync(c->probs_dev, c->probs.data(),
+                                  c->probs.size() * sizeof(fdlb::BatchProblem),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "problem table upload");
+  return FDLB_OK;
+}
+
+}  // namespace
+
+int fdlb_create_batch(int nprob, const int64_t* nx, const double* gamma, double x0, double x1,
+                      int Qphi, int Qchi, double tau, double dt, int precision, void* cuda_stream,
+                      fdlb_ctx** out) {
+  if (!out) return set_err(nullptr, FDLB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (nprob < 1 || !nx || !gamma) return set_err(nullptr, FDLB_EINVAL, "nprob < 1 or NULL arrays");
+  if (!(x1 > x0)) return set_err(nullptr, FDLB_EINVAL, "empty domain");
+  if (precision != FDLB_FP64 && precision != FDLB_MIXED)
+    return set_err(nullptr, FDLB_EINVAL, "precision must be FDLB_FP64 or FDLB_MIXED");
+  if (!((Qphi == 8 && Qchi == 8) || (Qphi == 5 && Qchi == 3)))
+    return set_err(nullptr, FDLB_EINVAL, "batch lattice Qphi=%d Qchi=%d not compiled", Qphi, Qchi);
+  if (!(tau > 0.0) || !(dt > 0.0)) return set_err(nullptr, FDLB_EINVAL, "tau and dt must be positive");
+  // lattice, coefficients and tables of the first problem; gas constants per problem
+  fdlb_grid g{1, nx[0], 1, x0, x1, 0.0, 1.0, FDLB_BC_OUTLET};
+  fdlb::DevParams tmpl{};
+  int rc = fdlb::params_for(&g, Qphi, Qchi, gamma[0], tau, dt, nullptr, &tmpl);
+  if (rc) return rc;
+  const double pmax = std::fmax(std::fabs(tmpl.pp[Qphi - 1]), std::fabs(tmpl.pc[Qchi - 1]));
+  std::vector<fdlb::BatchProblem> probs(nprob);
+  int64_t total = 0;
+  for (int i = 0; i < nprob; ++i) {
+    if (nx[i] < 1 || nx[i] > (1 << 28)) return set_err(nullptr, FDLB_EINVAL, "problem %d: bad nx", i);
+    const double gm = gamma[i];
+    if (!(gm > 1.0) || !std::isfinite(gm)) return set_err(nullptr, FDLB_EINVAL, "problem %d: gamma", i);
+    const double DK = 2.0 / (gm - 1.0);
+    if (DK - 1.0 < 0.0) return set_err(nullptr, FDLB_EINVAL, "problem %d: D+K-d < 0", i);
+    const double dx = (x1 - x0) / (double)nx[i];
+    if (pmax * dt / dx > 1.0)
+      return set_err(nullptr, FDLB_ECFL, "problem %d: CFL = %g > 1", i, pmax * dt / dx);
+    fdlb::BatchProblem& b = probs[i];
+    b = fdlb::BatchProblem{};
+    b.base = total;
+    b.nx = (int)nx[i];
+    b.kchi = DK - 1.0;
+    b.invDK = 1.0 / DK;
+    b.dtdx = dt / dx;
+    b.x0 = x0;
+    b.dx = dx;
+    b.xsplit = 0.5 * (x0 + x1);
+    total += nx[i];
+  }
+  if (total > ((int64_t)1 << 31) / 2) return set_err(nullptr, FDLB_EINVAL, "too many cells");
+  fdlb_ctx* c = new (std::nothrow) fdlb_ctx();
+  if (!c) return set_err(nullptr, FDLB_ENOMEM, "host allocation failed");
+  c->batch = true;
+  c->probs = probs;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->precision = precision;
+  c->tau = tau;
+  c->dt = dt;
+  c->grid = fdlb_grid{1, total, 1, x0, x1, 0.0, 1.0, FDLB_BC_OUTLET};
+  fdlb::DevParams& p = c->dp;
+  p = tmpl;
+  p.nx = (int)total;  // not used by the batch kernels (per-problem sizes)
+  p.N = total;
+  p.precision = precision;
+  p.nprob = nprob;
+  p.variant = 0;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_err(nullptr, e, "device query");
+  }
+  p.bgrid = 4 * c->nsm;
+  const size_t esize = precision == FDLB_MIXED ? sizeof(float) : sizeof(double);
+  const size_t arr = (size_t)p.P * (size_t)total * esize;
+  const size_t mom_bytes = 4 * (size_t)total * sizeof(double);
+  const size_t pstat_bytes = ((size_t)nprob * sizeof(unsigned) + 255) / 256 * 256;
+  c->buf_bytes = 6 * arr + mom_bytes + 256 + pstat_bytes;
+  e = cudaMalloc(&c->buf, c->buf_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&c->probs_dev, nprob * sizeof(fdlb::BatchProblem));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fdlb_destroy(c);
+    return set_err(nullptr, FDLB_ENOMEM, "batch allocation failed: %s", cudaGetErrorString(e));
+  }
+  char* b = (char*)c->buf;
+  p.F = b + 0 * arr;
+  p.F2 = b + 1 * arr;
+  p.F3 = b + 2 * arr;
+  p.A4 = b + 3 * arr;
+  p.Af = b + 4 * arr;
+  p.D = b + 5 * arr;
+  c->mom = (double*)(b + 6 * arr);
+  p.status = (unsigned*)(b + 6 * arr + mom_bytes);
+  p.pstatus = (unsigned*)(b + 6 * arr + mom_bytes + 256);
+  p.probs = c->probs_dev;
+  e = cudaMallocHost(&c->status_host, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->buf, 0, c->buf_bytes, c->stream);
+  if (e != cudaSuccess) {
+    int r = cuda_err(nullptr, e, "batch set-up");
+    fdlb_destroy(c);
+    return r;
+  }
+  if ((rc = upload_probs(c)) || (rc = upload_work(c))) {
+    std::string msg = c->err;
+    fdlb_destroy(c);
+    return set_err(nullptr, rc, "%s", msg.c_str());
+  }
+  *out = c;
+  return FDLB_OK;
+}
+
+int fdlb_batch_init_riemann(fdlb_ctx* c, const double* states, const double* xsplit) {
+  if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
+  if (!c->batch) return set_err(c, FDLB_EINVAL, "not a batch context");
+  if (!states) return set_err(c, FDLB_EINVAL, "states is NULL");
+  for (size_t i = 0; i < c->probs.size(); ++i) {
+    for (int q = 0; q < 2; ++q) {
+      const double* st = states + 6 * i + 3 * q;
+      if (!std::isfinite(st[0]) || !std::isfinite(st[1]) || !std::isfinite(st[2]) ||
+          !(st[0] > 0.0) || !(st[2] > 0.0))
+        return set_err(c, FDLB_EINVAL, "problem %zu: rho and P must be finite and > 0", i);
+      for (int j = 0; j < 3; ++j) c->probs[i].st[q][j] = st[j];
+    }
+    if (xsplit) c->probs[i].xsplit = xsplit[i];
+  }
+  int rc = upload_probs(c);
+  if (rc) return rc;
+  int e = fdlb::launch_batch_init(c->dp, c->stream);
+  if (e) return cuda_err(c, (cudaError_t)e, "batch init kernel launch");
+  c->prepared = false;
+  return ensure_prepared(c);
+}
+
+int fdlb_batch_status(fdlb_ctx* c, unsigned* flags) {
+  if (!c || !c->batch || !flags) return set_err(c, FDLB_EINVAL, "not a batch context or NULL");
+  cudaError_t e = cudaMemcpyAsync(flags, c->dp.pstatus, c->probs.size() * sizeof(unsigned),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_err(c, e, "fdlb_batch_status");
+  return FDLB_OK;
+}
+
+int fdlb_batch_offsets(const fdlb_ctx* c, int64_t* base) {
+  if (!c || !c->batch || !base) return set_err(nullptr, FDLB_EINVAL, "not a batch context");
+  for (size_t i = 0; i < c->probs.size(); ++i) base[i] = c->probs[i].base;
+  return FDLB_OK;
+}
+
+int fdlb_autotune(fdlb_ctx* c, int trial_steps, int* variant_out, int* ctas_per_sm_out) {
+  if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
+  if (!c->batch) return set_err(c, FDLB_EINVAL, "autotuning applies to batch contexts");
+  if (trial_steps < 1) trial_steps = 2;
+  int rc = ensure_prepared(c);
+  if (rc) return rc;
+  // keep the state: every trial starts from it
+  const size_t bytes = fdlb_state_bytes(c);
+  void* saved = nullptr;
+  cudaError_t e = cudaMalloc(&saved, bytes);
+  if (e != cudaSuccess) return set_err(c, FDLB_ENOMEM, "autotune buffer: %s", cudaGetErrorString(e));
+  e = cudaMemcpyAsync(saved, c->dp.F, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  const int ctas[] = {2, 4, 8, 16};
+  float best = 1e30f;
+  int best_v = 0, best_k = 4;
+  for (int v = 0; v < fdlb::kBatchVariants && e == cudaSuccess && !rc; ++v) {
+    c->dp.variant = v;
+    if ((rc = upload_work(c))) break;
+    for (int k : ctas) {
+      c->dp.bgrid = k * c->nsm;
+      e = cudaMemcpyAsync(c->dp.F, saved, bytes, cudaMemcpyDeviceToDevice, c->stream);
+      int le = e == cudaSuccess ? launch_stage_any(c, fdlb::kPrep, c->stream) : 0;
+      if (e == cudaSuccess) e = cudaEventRecord(t0, c->stream);
+      for (int s = 0; s < trial_steps && e == cudaSuccess && !le; ++s)
+        for (int st : {fdlb::kStage3, fdlb::kStage4, fdlb::kFinal})
+          if (!le) le = launch_stage_any(c, st, c->stream);
+      if (le) e = (cudaError_t)le;
+      if (e == cudaSuccess) e = cudaEventRecord(t1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_v = v;
+        best_k = k;
+      }
+    }
+  }
+  // restore the state and adopt the fastest shape
+  if (e == cudaSuccess && !rc) {
+    c->dp.variant = best_v;
+    c->dp.bgrid = best_k * c->nsm;
+    rc = upload_work(c);
+    if (!rc) e = cudaMemcpyAsync(c->dp.F, saved, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(saved);
+  drop_graph(c);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_err(c, e, "fdlb_autotune");
+  c->prepared = false;
+  rc = ensure_prepared(c);
+  if (rc) return rc;
+  if (variant_out) *variant_out = best_v;
+  if (ctas_per_sm_out) *ctas_per_sm_out = best_k;
+  return FDLB_OK;
+}
+
+int fdlb_batch_set_tiling(fdlb_ctx* c, int variant, int ctas_per_sm) {
+  if (!c || !c->batch) return set_err(c, FDLB_EINVAL, "not a batch context");
+  if (variant < 0 || variant >= fdlb::kBatchVariants || ctas_per_sm < 1 || ctas_per_sm > 64)
+    return set_err(c, FDLB_EINVAL, "variant in [0, %d), ctas_per_sm in [1, 64]", fdlb::kBatchVariants);
+  c->dp.variant = variant;
+  c->dp.bgrid = ctas_per_sm * c->nsm;
+  drop_graph(c);
+  return upload_work(c);
+}
+
 int fdlb_lattice_nodes(int Q, double* p, double* w) {
   if (!p || !w || Q < 1 || Q > kMaxQ) return set_err(nullptr, FDLB_EINVAL, "bad Q or NULL arrays");
   if (!gauss_hermite(Q, p, w)) return set_err(nullptr, FDLB_EINVAL, "Gauss-Hermite rule failed");
@@ -608,6 +920,10 @@ void fdlb_destroy(fdlb_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
+  drop_graph(c);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  if (c->probs_dev) cudaFree(c->probs_dev);
+  if (c->work_dev) cudaFree(c->work_dev);
   if (c->buf) cudaFree(c->buf);
   if (c->status_host) cudaFreeHost(c->status_host);
   delete c;

@@ -29,6 +29,25 @@ struct StageCoef {
   double c2;                    // F2 = F_eq + c2 (F - F_eq)
 };
 
+// One 1-D problem of a batch (fdlb_create_batch): its cells occupy
+// [base, base + nx) of the concatenated population arrays.
+struct BatchProblem {
+  int64_t base;
+  int nx;
+  int pad_;
+  double kchi, invDK;   // D+K-d and 1/(D+K) of this problem's gamma
+  double dtdx;          // dt / dx
+  double x0, dx;        // domain start and cell size
+  double xsplit;        // membrane of the Riemann data
+  double st[2][3];      // (rho, u, P) left and right
+};
+
+// One tile of the batch work list: problem index and first cell.
+struct WorkItem {
+  int prob;
+  int x0;
+};
+
 // Everything a stage kernel needs; passed by value as a __grid_constant__
 // kernel parameter (about 14 KB).
 struct DevParams {
@@ -55,7 +74,19 @@ struct DevParams {
   void* Af;     // running explicit part of F^{n+1}
   void* D;      // F^n - F^n_eq
   unsigned* status;  // bit 0: invalid moments seen
+  // batches of 1-D problems (nprob > 0): N is the total cell count
+  const BatchProblem* probs;
+  const WorkItem* work;
+  unsigned* pstatus;  // per problem: bit 0 invalid moments seen
+  int nprob, nwork;
+  int variant;  // 1-D tile shape of the batch kernels (0, 1, 2)
+  int bgrid;    // persistent grid size of the batch kernels
 };
+
+// 1-D tile shapes of the batch kernels, indexed by DevParams::variant:
+// cells per tile and CTAs per SM of the persistent grid are the tuning knobs.
+constexpr int kBatchVariants = 3;
+int batch_tile_cells(int variant);
 
 enum Stage { kPrep = 0, kStage3 = 1, kStage4 = 2, kFinal = 3 };
 
@@ -67,5 +98,8 @@ int launch_init_riemann(const DevParams& p, const double* states, int nq, double
                         cudaStream_t s);
 int launch_moments(const DevParams& p, double* n, double* ux, double* uy, double* T,
                    cudaStream_t s);
+// batch kernels (d = 1, several problems in one launch)
+int launch_batch_stage(const DevParams& p, int stage, cudaStream_t s);
+int launch_batch_init(const DevParams& p, cudaStream_t s);
 
 }  // namespace fdlb

@@ -27,19 +27,50 @@ namespace {
 
 constexpr int H = 5;  // ghost nodes per side (Sec. IV)
 
-template <int DIM>
+template <int DIM, int VAR = 0>
 struct TileCfg;
 // 2-D: 16 x 16 cells, 4 populations per group; 128 threads march the 4 x 32
 // tile lines (16 along x, 16 along y) of a group, one line each.
 template <>
-struct TileCfg<2> {
+struct TileCfg<2, 0> {
   static constexpr int TX = 16, TY = 16, NT = 128, G = 4, SEG = TX + 1;
 };
 // 1-D: 127 cells, 8 populations per group; 128 threads march 16 segments of
 // 8 interfaces of each of the 8 lines.
 template <>
-struct TileCfg<1> {
+struct TileCfg<1, 0> {
   static constexpr int TX = 127, TY = 1, NT = 128, G = 8, SEG = 8;
+};
+// 1-D: 63 cells, 16 populations per group, 8 segments of 8 interfaces.
+template <>
+struct TileCfg<1, 1> {
+  static constexpr int TX = 63, TY = 1, NT = 128, G = 16, SEG = 8;
+};
+// 1-D: 255 cells, 8 populations per group, 16 segments of 16 interfaces.
+template <>
+struct TileCfg<1, 2> {
+  static constexpr int TX = 255, TY = 1, NT = 128, G = 8, SEG = 16;
+};
+
+// Shared memory of one tile: the advected populations of a group on tile +
+// halo, and the interface values along x and y.
+template <int DIM, typename S, int VAR>
+struct TileSmem {
+  using C = TileCfg<DIM, VAR>;
+  static constexpr int SX = C::TX + 2 * 5 + (DIM == 2 ? 1 : 0);  // padded row pitch (2-D)
+  static constexpr int SY = DIM == 2 ? C::TY + 2 * 5 : 1;
+  S tile[C::G][SY][SX];
+  S hx[C::G][C::TY][C::TX + 1];
+  S hy[DIM == 2 ? C::G : 1][DIM == 2 ? C::TX : 1][C::TY + 1];
+};
+
+// Where a tile lives: its problem's size, first cell in the population
+// arrays, and gas and grid constants.
+struct Geo {
+  int nx, ny;
+  int64_t base;
+  double kchi, invDK, dtdx, dtdy;
+  int prob;  // batch problem index, -1 for a single-problem context
 };
 
 __device__ __forceinline__ int wrap_or_clamp(int i, int n, int bc) {
@@ -114,14 +145,14 @@ struct EqCell {
 
 // Factors from (n, u, T); phi^eq = n prod g, chi^eq = (D+K-d) T n prod g^chi.
 template <int DIM, int QP, int QC>
-__device__ __forceinline__ void make_eq_nut(const DevParams& p, double n, double ux, double uy,
-                                            double T, EqCell<DIM, QP, QC>& eq) {
+__device__ __forceinline__ void make_eq_nut(const DevParams& p, double kchi, double n, double ux,
+                                            double uy, double T, EqCell<DIM, QP, QC>& eq) {
   double gx[QP];
   axis_g<QP>(p.wHp, ux, T, gx);
 #pragma unroll
   for (int k = 0; k < QP; ++k) eq.hp[k] = n * gx[k];
   if constexpr (DIM == 2) axis_g<QP>(p.wHp, uy, T, eq.gyp);
-  const double nchi = p.kchi * T * n;
+  const double nchi = kchi * T * n;
   if constexpr (QC == QP) {
 #pragma unroll
     for (int k = 0; k < QC; ++k) eq.hc[k] = nchi * gx[k];
@@ -141,13 +172,13 @@ __device__ __forceinline__ void make_eq_nut(const DevParams& p, double n, double
 // n, u and T = (sum phi p^2 + sum chi - n u^2) / ((D+K) n) from the moment
 // sums; false if the cell is not a valid gas state.
 template <int DIM>
-__device__ __forceinline__ bool moments_to_nut(const DevParams& p, const Moments& m, double& n,
+__device__ __forceinline__ bool moments_to_nut(double invDK, const Moments& m, double& n,
                                                double& ux, double& uy, double& T) {
   n = m.n;
   const double inv_n = 1.0 / n;
   ux = m.jx * inv_n;
   uy = DIM == 2 ? m.jy * inv_n : 0.0;
-  T = (m.e - n * fma(ux, ux, uy * uy)) * inv_n * p.invDK;
+  T = (m.e - n * fma(ux, ux, uy * uy)) * inv_n * invDK;
   return (n > 0.0) && (T > 0.0) && isfinite(n) && isfinite(T) && isfinite(ux) && isfinite(uy);
 }
 
@@ -255,14 +286,16 @@ struct CoefS {
         a43e3((S)c.a43e3), w3e3((S)c.w3e3), a44e4((S)c.a44e4), w4e4((S)c.w4e4), c2((S)c.c2) {}
 };
 
-template <int DIM, int QP, int QC, int STAGE, typename S>
-__global__ void __launch_bounds__(TileCfg<DIM>::NT)
-    stage_kernel(const __grid_constant__ DevParams p) {
-  using C = TileCfg<DIM>;
+// One tile (origin x0, y0 of problem g) of one fused stage; see the file
+// header for the two passes.  Ends with every thread past its last use of
+// the shared memory, so a persistent CTA may start its next tile at once.
+template <int DIM, int QP, int QC, int STAGE, typename S, int VAR>
+__device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, int x0, int y0,
+                                           TileSmem<DIM, S, VAR>& sm) {
+  using C = TileCfg<DIM, VAR>;
   using L = Lat<DIM, QP, QC>;
   constexpr int TX = C::TX, TY = C::TY, NT = C::NT, G = C::G, SEG = C::SEG;
-  constexpr int SX = TX + 2 * H + (DIM == 2 ? 1 : 0);  // padded row pitch (2-D)
-  constexpr int SY = DIM == 2 ? TY + 2 * H : 1;
+  constexpr int SX = TileSmem<DIM, S, VAR>::SX;
   constexpr int CELLS = TX * TY;
   constexpr int CPT = (CELLS + NT - 1) / NT;
   constexpr int NSEG = (TX + 1) / SEG;  // segments per line
@@ -270,9 +303,10 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
   constexpr int NLINE = DIM == 2 ? TX + TY : 1;
   static_assert(G * NLINE * NSEG == NT, "one march task per thread");
 
-  __shared__ S tile[G][SY][SX];
-  __shared__ S hx[G][TY][TX + 1];
-  __shared__ S hy[DIM == 2 ? G : 1][DIM == 2 ? TX : 1][TY + 1];
+  constexpr int SY = TileSmem<DIM, S, VAR>::SY;
+  auto& tile = sm.tile;
+  auto& hx = sm.hx;
+  auto& hy = sm.hy;
   S* __restrict__ const F = (S*)p.F;
   S* __restrict__ const F2 = (S*)p.F2;
   S* __restrict__ const F3 = (S*)p.F3;
@@ -281,9 +315,7 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
   S* __restrict__ const Dn = (S*)p.D;
 
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX;
-  const int y0 = blockIdx.y * TY;
-  const int64_t N = p.N;
+  const int64_t N = p.N;  // population stride
 
   int lxs[CPT], lys[CPT];
   int64_t cell[CPT];
@@ -294,8 +326,8 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
     lxs[k] = c % TX;
     lys[k] = c / TX;
     const int x = x0 + lxs[k], y = y0 + lys[k];
-    valid[k] = (c < CELLS) && (x < p.nx) && (y < p.ny);
-    cell[k] = (int64_t)y * p.nx + x;
+    valid[k] = (c < CELLS) && (x < geo.nx) && (y < geo.ny);
+    cell[k] = geo.base + (int64_t)y * geo.nx + x;
   }
   typename MomAcc<S>::type mom[CPT];
 #pragma unroll
@@ -324,9 +356,9 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
         const int pop = g0 + g;
         S v = 0;
         if (pop < L::P && cidx < TX + 2 * H) {
-          const int gx = wrap_or_clamp(x0 - H + cidx, p.nx, p.bc);
-          const int gy = (DIM == 2) ? wrap_or_clamp(y0 - H + r, p.ny, p.bc) : 0;
-          v = adv[pop * N + (int64_t)gy * p.nx + gx];
+          const int gx = wrap_or_clamp(x0 - H + cidx, geo.nx, p.bc);
+          const int gy = (DIM == 2) ? wrap_or_clamp(y0 - H + r, geo.ny, p.bc) : 0;
+          v = adv[pop * N + geo.base + (int64_t)gy * geo.nx + gx];
         }
         tile[g][r][cidx] = v;
       }
@@ -363,8 +395,9 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
           const int pop = g0 + g;
           if (pop >= L::P) break;
           // X = dt * (p . grad F) = dt p_x (Fhat_{x+1/2} - Fhat_{x-1/2})/dx + (y)
-          S X = (S)p.cx[pop] * (hx[g][ly][lx + 1] - hx[g][ly][lx]);
-          if constexpr (DIM == 2) X = sfma((S)p.cy[pop], hy[g][lx][ly + 1] - hy[g][lx][ly], X);
+          S X = (S)(geo.dtdx * p.px[pop]) * (hx[g][ly][lx + 1] - hx[g][ly][lx]);
+          if constexpr (DIM == 2)
+            X = sfma((S)(geo.dtdy * p.py[pop]), hy[g][lx][ly + 1] - hy[g][lx][ly], X);
           const int64_t e = pop * N + cell[k];
           S R;
           if (STAGE == kStage3) {
@@ -393,9 +426,12 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
   for (int k = 0; k < CPT; ++k) {
     if (!valid[k]) continue;
     double n, ux, uy, T;
-    if (!moments_to_nut<DIM>(p, to_fp64(mom[k]), n, ux, uy, T)) atomicOr(p.status, 1u);
+    if (!moments_to_nut<DIM>(geo.invDK, to_fp64(mom[k]), n, ux, uy, T)) {
+      atomicOr(p.status, 1u);
+      if (geo.prob >= 0) atomicOr(&p.pstatus[geo.prob], 1u);
+    }
     EqCell<DIM, QP, QC> eq64;
-    make_eq_nut<DIM, QP, QC>(p, n, ux, uy, T, eq64);
+    make_eq_nut<DIM, QP, QC>(p, geo.kchi, n, ux, uy, T, eq64);
     EqCellS<DIM, QP, QC, S> eq;
     to_storage(eq64, eq);
     const int64_t c = cell[k];
@@ -422,6 +458,60 @@ __global__ void __launch_bounds__(TileCfg<DIM>::NT)
       }
     }
   }
+}
+
+// One tile per CTA, the grid covering one problem.
+template <int DIM, int QP, int QC, int STAGE, typename S>
+__global__ void __launch_bounds__(TileCfg<DIM>::NT)
+    stage_kernel(const __grid_constant__ DevParams p) {
+  __shared__ TileSmem<DIM, S, 0> sm;
+  const Geo geo{p.nx, p.ny, 0, p.kchi, p.invDK, p.dtdx, p.dtdy, -1};
+  stage_tile<DIM, QP, QC, STAGE, S, 0>(p, geo, blockIdx.x * TileCfg<DIM>::TX,
+                                       blockIdx.y * TileCfg<DIM>::TY, sm);
+}
+
+// Batches of 1-D problems: a persistent grid walks the tile work list of all
+// problems (each tile within one problem, ghosts clamped at its own ends).
+template <int QP, int QC, int STAGE, typename S, int VAR>
+__global__ void __launch_bounds__(TileCfg<1, VAR>::NT)
+    batch_stage_kernel(const __grid_constant__ DevParams p) {
+  __shared__ TileSmem<1, S, VAR> sm;
+  for (int w = blockIdx.x; w < p.nwork; w += gridDim.x) {
+    const WorkItem it = p.work[w];
+    const BatchProblem& bp = p.probs[it.prob];
+    const Geo geo{bp.nx, 1, bp.base, bp.kchi, bp.invDK, bp.dtdx, 0.0, it.prob};
+    stage_tile<1, QP, QC, STAGE, S, VAR>(p, geo, it.x0, 0, sm);
+  }
+}
+
+// problem of cell c (problems sorted by base)
+__device__ __forceinline__ int find_problem(const DevParams& p, int64_t c) {
+  int lo = 0, hi = p.nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (p.probs[mid].base <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int QP, int QC, typename S>
+__global__ void batch_init_kernel(const __grid_constant__ DevParams p) {
+  using L = Lat<1, QP, QC>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const BatchProblem& bp = p.probs[find_problem(p, c)];
+  const int x = (int)(c - bp.base);
+  const double xc = bp.x0 + (x + 0.5) * bp.dx;
+  const int q = (xc >= bp.xsplit) ? 1 : 0;
+  const double rho = bp.st[q][0], ux = bp.st[q][1], P = bp.st[q][2];
+  EqCell<1, QP, QC> eq64;
+  make_eq_nut<1, QP, QC>(p, bp.kchi, rho, ux, 0.0, P / rho, eq64);
+  EqCellS<1, QP, QC, double> eq;
+  to_storage(eq64, eq);
+  S* F = (S*)p.F;
+#pragma unroll
+  for (int pop = 0; pop < L::P; ++pop) F[pop * p.N + c] = (S)feq_of<1, QP, QC, double>(eq, pop);
 }
 
 // Piecewise-constant Riemann data -> discrete equilibrium (Sec. V).
@@ -451,7 +541,7 @@ __global__ void init_riemann_kernel(const __grid_constant__ DevParams p,
   const double uy = DIM == 2 ? a.st[q][2] : 0.0;
   const double P = a.st[q][DIM == 2 ? 3 : 2];
   EqCell<DIM, QP, QC> eq64;
-  make_eq_nut<DIM, QP, QC>(p, rho, ux, uy, P / rho, eq64);
+  make_eq_nut<DIM, QP, QC>(p, p.kchi, rho, ux, uy, P / rho, eq64);
   EqCellS<DIM, QP, QC, double> eq;  // binary64 products, rounded once on store
   to_storage(eq64, eq);
   S* F = (S*)p.F;
@@ -470,7 +560,8 @@ __global__ void moments_kernel(const __grid_constant__ DevParams p, double* __re
   const S* F = (const S*)p.F;
   for (int pop = 0; pop < L::P; ++pop) accumulate<DIM, QP, QC>(p, m, pop, F[pop * p.N + c]);
   double nn, vx, vy, TT;
-  moments_to_nut<DIM>(p, to_fp64(m), nn, vx, vy, TT);
+  const double invDK = p.nprob > 0 ? p.probs[find_problem(p, c)].invDK : p.invDK;
+  moments_to_nut<DIM>(invDK, to_fp64(m), nn, vx, vy, TT);
   n[c] = nn;
   ux[c] = vx;
   if (DIM == 2 && uy) uy[c] = vy;
@@ -514,6 +605,48 @@ int launch_moments_t(const DevParams& p, double* n, double* ux, double* uy, doub
   else moments_kernel<DIM, QP, QC, double><<<(unsigned)nb, nt, 0, s>>>(p, n, ux, uy, T);
   return (int)cudaGetLastError();
 }
+
+template <int QP, int QC, typename S, int VAR>
+int launch_batch_stage_v(const DevParams& p, int stage, cudaStream_t s) {
+  using C = TileCfg<1, VAR>;
+  const int grid = p.bgrid > 0 ? p.bgrid : 1;
+  switch (stage) {
+    case kPrep: batch_stage_kernel<QP, QC, kPrep, S, VAR><<<grid, C::NT, 0, s>>>(p); break;
+    case kStage3: batch_stage_kernel<QP, QC, kStage3, S, VAR><<<grid, C::NT, 0, s>>>(p); break;
+    case kStage4: batch_stage_kernel<QP, QC, kStage4, S, VAR><<<grid, C::NT, 0, s>>>(p); break;
+    default: batch_stage_kernel<QP, QC, kFinal, S, VAR><<<grid, C::NT, 0, s>>>(p); break;
+  }
+  return (int)cudaGetLastError();
+}
+
+template <int QP, int QC, typename S>
+int launch_batch_stage_s(const DevParams& p, int stage, cudaStream_t s) {
+  switch (p.variant) {
+    case 1: return launch_batch_stage_v<QP, QC, S, 1>(p, stage, s);
+    case 2: return launch_batch_stage_v<QP, QC, S, 2>(p, stage, s);
+    default: return launch_batch_stage_v<QP, QC, S, 0>(p, stage, s);
+  }
+}
+
+template <int QP, int QC>
+int launch_batch_stage_t(const DevParams& p, int stage, cudaStream_t s) {
+  return p.precision == 1 ? launch_batch_stage_s<QP, QC, float>(p, stage, s)
+                          : launch_batch_stage_s<QP, QC, double>(p, stage, s);
+}
+
+template <int QP, int QC>
+int launch_batch_init_t(const DevParams& p, cudaStream_t s) {
+  const int nt = 128;
+  const int64_t nb = (p.N + nt - 1) / nt;
+  if (p.precision == 1) batch_init_kernel<QP, QC, float><<<(unsigned)nb, nt, 0, s>>>(p);
+  else batch_init_kernel<QP, QC, double><<<(unsigned)nb, nt, 0, s>>>(p);
+  return (int)cudaGetLastError();
+}
+
+// Lattices of the batch kernels (1-D).
+#define FDLB_BATCH_LATTICES(X) \
+  X(8, 8)                      \
+  X(5, 3)
 
 // Dispatch over the compiled (d, Qphi, Qchi) instances.
 #define FDLB_LATTICES(X) \
@@ -568,6 +701,30 @@ int launch_moments(const DevParams& p, double* n, double* ux, double* uy, double
 #define X(D_, P_, C_) \
   if (p.d == D_ && p.Qp == P_ && p.Qc == C_) return launch_moments_t<D_, P_, C_>(p, n, ux, uy, T, s);
   FDLB_LATTICES(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int batch_tile_cells(int variant) {
+  switch (variant) {
+    case 1: return TileCfg<1, 1>::TX;
+    case 2: return TileCfg<1, 2>::TX;
+    default: return TileCfg<1, 0>::TX;
+  }
+}
+
+int launch_batch_stage(const DevParams& p, int stage, cudaStream_t s) {
+#define X(P_, C_) \
+  if (p.Qp == P_ && p.Qc == C_) return launch_batch_stage_t<P_, C_>(p, stage, s);
+  FDLB_BATCH_LATTICES(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_batch_init(const DevParams& p, cudaStream_t s) {
+#define X(P_, C_) \
+  if (p.Qp == P_ && p.Qc == C_) return launch_batch_init_t<P_, C_>(p, s);
+  FDLB_BATCH_LATTICES(X)
 #undef X
   return (int)cudaErrorInvalidValue;
 }

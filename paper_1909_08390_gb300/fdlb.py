@@ -86,6 +86,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fdlb_set_stream.argtypes = [_vp, _vp]
     lib.fdlb_launches_per_step.argtypes = [_vp]
     lib.fdlb_lattice_nodes.argtypes = [ctypes.c_int, _dp, _dp]
+    _i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.fdlb_create_batch.argtypes = [ctypes.c_int, _i64p, _dp, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+    lib.fdlb_batch_init_riemann.argtypes = [_vp, _dp, _dp]
+    lib.fdlb_batch_offsets.argtypes = [_vp, _i64p]
+    lib.fdlb_batch_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint)]
+    lib.fdlb_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int)]
+    lib.fdlb_batch_set_tiling.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
     lib.fdlb_step_noalloc.argtypes = [ctypes.POINTER(fdlb_grid), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.POINTER(fdlb_tableau), _vp, ctypes.c_int64, _vp]
@@ -209,6 +219,49 @@ def fdlb_step_noalloc(grid: fdlb_grid, Qphi: int, Qchi: int, gamma: float, tau: 
     _check(rc, None)
 
 
+def fdlb_create_batch(nx, gamma, x0: float, x1: float, Qphi: int, Qchi: int, tau: float,
+                      dt: float, precision: int = FDLB_MIXED, stream=None):
+    nxa = np.ascontiguousarray(nx, dtype=np.int64)
+    ga = np.ascontiguousarray(gamma, dtype=np.float64)
+    assert nxa.shape == ga.shape
+    out = _vp()
+    rc = load().fdlb_create_batch(int(nxa.size), nxa.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  ga.ctypes.data_as(_dp), float(x0), float(x1), int(Qphi), int(Qchi),
+                                  float(tau), float(dt), int(precision), _stream_handle(stream),
+                                  ctypes.byref(out))
+    _check(rc, None)
+    return out
+
+
+def fdlb_batch_init_riemann(ctx, states, xsplit=None):
+    st = np.ascontiguousarray(states, dtype=np.float64)
+    xs = None if xsplit is None else np.ascontiguousarray(xsplit, dtype=np.float64)
+    _check(load().fdlb_batch_init_riemann(ctx, st.ctypes.data_as(_dp),
+                                          None if xs is None else xs.ctypes.data_as(_dp)), ctx)
+
+
+def fdlb_batch_offsets(ctx, nprob: int):
+    base = np.zeros(nprob, dtype=np.int64)
+    _check(load().fdlb_batch_offsets(ctx, base.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), ctx)
+    return base
+
+
+def fdlb_batch_status(ctx, nprob: int):
+    flags = np.zeros(nprob, dtype=np.uint32)
+    _check(load().fdlb_batch_status(ctx, flags.ctypes.data_as(ctypes.POINTER(ctypes.c_uint))), ctx)
+    return flags
+
+
+def fdlb_autotune(ctx, trial_steps: int = 2):
+    v, k = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().fdlb_autotune(ctx, int(trial_steps), ctypes.byref(v), ctypes.byref(k)), ctx)
+    return v.value, k.value
+
+
+def fdlb_batch_set_tiling(ctx, variant: int, ctas_per_sm: int):
+    _check(load().fdlb_batch_set_tiling(ctx, int(variant), int(ctas_per_sm)), ctx)
+
+
 def fdlb_destroy(ctx):
     if ctx:
         load().fdlb_destroy(ctx)
@@ -304,3 +357,43 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+class BatchSolver(Solver):
+    """Independent 1-D problems in one context (fdlb_create_batch)."""
+
+    def __init__(self, nx, gamma, x0: float = -0.5, x1: float = 0.5, Qphi: int = 8, Qchi: int = 8,
+                 tau: float = 1e-6, dt: float = 2e-5, precision: int = FDLB_MIXED, stream=None):
+        self.d, self.ny = 1, 1
+        self.nprob = len(nx)
+        self.nxs = np.asarray(nx, dtype=np.int64)
+        self.ctx = fdlb_create_batch(nx, gamma, x0, x1, Qphi, Qchi, tau, dt, precision, stream)
+        self.P = fdlb_npop(self.ctx)
+        self.N = fdlb_ncells(self.ctx)
+        self.nx = self.N
+        self.precision = precision
+        self.dtype = np.float32 if precision == FDLB_MIXED else np.float64
+        self.base = fdlb_batch_offsets(self.ctx, self.nprob)
+
+    def init_riemann(self, states, xsplit=None):
+        fdlb_batch_init_riemann(self.ctx, states, xsplit)
+
+    def autotune(self, trial_steps: int = 2):
+        return fdlb_autotune(self.ctx, trial_steps)
+
+    def status(self):
+        """Per-problem flags (bit 0: the problem went unstable)."""
+        return fdlb_batch_status(self.ctx, self.nprob)
+
+    def step(self, nsteps: int = 1, allow_unstable: bool = False):
+        """Advance; with allow_unstable, a member that went unstable does not
+        raise (check status())."""
+        try:
+            fdlb_step(self.ctx, nsteps)
+        except FdlbError as e:
+            if not (allow_unstable and e.code == FDLB_EUNSTABLE):
+                raise
+
+    def member(self, arr, i):
+        """Slice of problem i from a concatenated per-cell array (last axis)."""
+        return arr[..., self.base[i]:self.base[i] + self.nxs[i]]
