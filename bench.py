@@ -222,6 +222,64 @@ def run_reference(args, world, rank):
     return 0
 
 
+def adjoint_cost(fdlb, stream):
+    """Times, on the 2048-cell differentiable run (Q = 8, gamma = 7/5,
+    tau = 1e-5, dt = 2e-5, 2000 steps, checkpoints every 50): the plain
+    forward steps, the checkpointed forward and the reverse pass (segment
+    recomputation + the three adjoint stage kernels per step); median of 3."""
+    import torch
+    from paper_1909_08390_gb300 import workloads as W
+    run = W.adjoint_1d()
+    spec = run.spec()
+    prm = torch.as_tensor(run.params(), device="cuda")
+    n0, u0, T0 = fdlb.blended_fields(prm, run.nx, run.x0, run.x1, run.width)
+    ctx, Qphi = fdlb._field_context(spec, run.gamma, run.tau, n0, u0, T0)
+    try:
+        P = fdlb.fdlb_npop(ctx)
+        start = torch.empty((P, run.nx), dtype=torch.float64, device="cuda")
+        fdlb.fdlb_get_state(ctx, start, True)
+        ck = torch.empty((run.nsteps // run.every + 1, P, run.nx), dtype=torch.float64,
+                         device="cuda")
+        Fbar = torch.zeros((P, run.nx), dtype=torch.float64, device="cuda")
+
+        def timed(fn, reps=3):
+            ms = []
+            for _ in range(reps):
+                fdlb.fdlb_set_state(ctx, start, True)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return statistics.median(ms)
+
+        fdlb.fdlb_step(ctx, 64)  # warm-up (graph capture, first launches)
+        fwd = timed(lambda: fdlb.fdlb_step(ctx, run.nsteps))
+        ckf = timed(lambda: fdlb.fdlb_forward_ckpt(ctx, run.nsteps, run.every, ck))
+
+        def reverse():
+            Fbar.zero_()
+            Fbar[:Qphi] = 1.0
+            fdlb.fdlb_adjoint(ctx, run.nsteps, run.every, ck, Fbar)
+
+        reverse()  # work space allocation
+        rev = timed(reverse)
+    finally:
+        fdlb.fdlb_destroy(ctx)
+    return {
+        "workload": "1-D blended shock tube, 2048 cells, Q=8 (16 populations), gamma=7/5, "
+                    "tau=1e-5, dt=2e-5, 2000 steps, checkpoints every 50, FP64",
+        "forward_ms_per_step": fwd / run.nsteps,
+        "checkpointed_forward_ms_per_step": ckf / run.nsteps,
+        "reverse_ms_per_step": rev / run.nsteps,
+        "reverse_over_forward": rev / fwd,
+        "forward_plus_reverse_over_forward": (ckf + rev) / fwd,
+        "gpu_launches_reverse_per_step": 6,
+    }
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -388,6 +446,13 @@ def run_ours(args, world, rank, local):
             "gpu_launches": 3 * args.steps,
         }
 
+    # discrete adjoint (1-D, binary64): the differentiable 2048-cell run of
+    # 2000 steps with checkpoints every 50 steps; cost of the reverse pass
+    # against the plain forward steps of the same problem
+    adjoint = None
+    if not args.no_adjoint and world == 1:
+        adjoint = adjoint_cost(fdlb, stream)
+
     # end to end through the C ABI with host buffers: per step, upload the
     # state from pinned host memory, advance one step, read the moments back.
     host_state = torch.empty(s.shape, dtype=torch.float64, pin_memory=True)
@@ -425,7 +490,7 @@ def run_ours(args, world, rank, local):
                    "cells": int(N), "populations": int(P), "parallelism": f"replicas{world}",
                    "l2": "working set 1.6 GB > 129 MB L2 (no flush needed)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
-        "batched": batched,
+        "batched": batched, "adjoint": adjoint,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
@@ -447,6 +512,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = _dist_setup()

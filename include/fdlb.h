@@ -190,6 +190,39 @@ int fdlb_autotune(fdlb_ctx* ctx, int trial_steps, int* variant_out, int* ctas_pe
 /* Set the batch tile shape directly (variant 0, 1, 2 = 127, 63, 255 cells). */
 int fdlb_batch_set_tiling(fdlb_ctx* ctx, int variant, int ctas_per_sm);
 
+/* ---- adjoint (1-D binary64 contexts with outlet ghosts and Table I) --------
+ * Gradients of a loss of the final state with respect to the initial fields,
+ * gamma and tau, by the discrete adjoint of the IMEX step: hand-written
+ * kernels applying, in reverse stage order, the transposes of the step's
+ * operations, with the MP limiter's choices frozen as the forward pass made
+ * them (recomputed from the saved forward stage states), and the exact
+ * Jacobian of the equilibria (Eq. gExpanded) with respect to the moments.
+ * Checkpoints every `every` steps; each segment is recomputed once. */
+
+/* F = discrete equilibrium of the per-cell fields n, u, T (device arrays of
+ * ncells doubles). */
+int fdlb_init_fields(fdlb_ctx* ctx, const double* n, const double* u, const double* T);
+
+/* Adjoint of fdlb_init_fields: given Fbar (device, state layout), the fields'
+ * adjoints nbar, ubar, Tbar (device arrays) and the contribution to
+ * d/dgamma through chi^eq = (D+K-d) T phi^eq (*dgamma, host). */
+int fdlb_init_fields_adjoint(fdlb_ctx* ctx, const double* Fbar, const double* n, const double* u,
+                             const double* T, double* nbar, double* ubar, double* Tbar,
+                             double* dgamma);
+
+/* Advance nsteps from the current state, storing the state before steps
+ * 0, every, 2 every, ... into ckpt (device, (nsteps/every + 1) states). */
+int fdlb_forward_ckpt(fdlb_ctx* ctx, int64_t nsteps, int every, void* ckpt);
+
+/* Reverse pass over the nsteps steps whose checkpoints fdlb_forward_ckpt
+ * stored: Fbar (device, state layout) holds dLoss/dF(nsteps) on entry and
+ * dLoss/dF(0) on return; dparams (host, 2) receives the step contributions
+ * dLoss/dgamma and dLoss/dtau.  The context's state is left as it was.
+ * Allocates its work space (4 every + 9 states) on first use; the context's
+ * derived scratch arrays are rebuilt from its state before it returns. */
+int fdlb_adjoint(fdlb_ctx* ctx, int64_t nsteps, int every, const void* ckpt, double* Fbar,
+                 double* dparams);
+
 /* The Gauss-Hermite rule of order Q (1 <= Q <= 16) the library uses for
  * weight exp(-p^2/2)/sqrt(2 pi): p[0..Q-1] the roots of He_Q in ascending
  * order, w[0..Q-1] = Q!/He_{Q+1}(p_k)^2 (Sec. II).  Host arrays; no GPU

@@ -1,0 +1,811 @@
+// fdlb_adjoint.cu -- discrete adjoint of the binary64 1-D IMEX step, hand
+// written, with the MP limiter's selections frozen from the forward pass.
+//
+// Forward step (fused form, see fdlb_internal.h), per population array:
+//   E0 = Feq(mom(F)), D = F - E0, F2 = E0 + c2 D, X2 = dt L(F2)
+//   R3 = F - k3 D - at32 X2,  E3 = Feq(mom(R3)),  D3 = R3 - E3
+//   F3 = R3 - a33e3 D3,  A4 = F - k4 D - at42 X2 - a43e3 D3,
+//   Af = F - kf D - wt2 X2 - w3e3 D3,  X3 = dt L(F3)
+//   R4 = A4 - at43 X3,  E4 = Feq(mom(R4)),  D4 = R4 - E4
+//   F4 = R4 - a44e4 D4,  Af2 = Af - wt3 X3 - w4e4 D4,  X4 = dt L(F4)
+//   F' = Af2 - wt4 X4.
+// With the limiter's choices fixed, L is linear: each interface value is
+// F_s plus one of the candidate offsets of Sec. IV (F^L - F_s, or a bound:
+// 0, F_{s+1} - F_s, F^MD - F_s, F^UL - F_s, F^LC - F_s, with the four-way
+// minmod choices inside F^MD and F^LC), each a fixed linear combination of
+// the 9-cell window.  The adjoint kernels recompute those choices from the
+// saved forward stage input with the forward's own integer-key comparisons
+// and apply the transpose.  mom and Feq (Eq. Moments_discrete and
+// Eq. gExpanded) are differentiated exactly: with a_l(u, T) the Hermite
+// coefficients, da_l/du = l a_{l-1} and da_l/dT = l(l-1)/2 a_{l-2}.
+// One adjoint kernel per advected stage (adj4, adj3, adj2) runs in reverse.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "fdlb.h"
+#include "fdlb_ctx.h"
+#include "fdlb_internal.h"
+#include "fdlb_mp9.cuh"
+
+namespace fdlb {
+namespace {
+
+constexpr int kTX = 16;   // cells per adjoint tile
+constexpr int kNT = 128;  // threads per adjoint CTA
+constexpr int kNI = kTX + 11;  // interfaces whose windows reach the tile: [x0-5, x0+TX+5]
+
+// Scalar accumulators of the adjoint (binary64, device):
+enum AdjScalar {
+  kBarC2 = 0, kBarK3, kBarK4, kBarKf, kBarA33e3, kBarA43e3, kBarW3e3, kBarA44e4, kBarW4e4,
+  kBarDK, kNumAdjScalars
+};
+
+struct AdjParams {
+  const double* Fn;    // F^n of the step
+  const double* F2s;   // stage-2 populations
+  const double* F3s;   // stage-3 populations
+  const double* F4s;   // stage-4 populations
+  const double* Gbar;  // adjoint of F^{n+1}
+  double* A4bar;       // adjoint of A4
+  double* X3bar;       // adjoint of X3
+  double* X2bar;       // adjoint of X2
+  double* Fpart;       // direct part of the adjoint of F^n
+  double* Dbar;        // adjoint of D
+  double* Gnew;        // adjoint of F^n (output; may alias Gbar)
+  double* scal;        // kNumAdjScalars accumulators
+};
+
+// ---- frozen-limiter interface: value coefficients over the window ----------
+
+// four-argument minmod choice as made by minmod4_bits: index 0..3 of the
+// chosen argument, or -1 for zero
+__device__ __forceinline__ int minmod4_choice(long long a, long long b, long long c, long long d) {
+  const bool same = ((a ^ b) >= 0) && ((a ^ c) >= 0) && ((a ^ d) >= 0);
+  const long long ma = a & kMag, mb = b & kMag, mc = c & kMag, md = d & kMag;
+  const bool nz = (ma != 0) && (mb != 0) && (mc != 0) && (md != 0);
+  int r = 0;
+  long long mr = ma;
+  if (mb < mr) { r = 1; mr = mb; }
+  if (mc < mr) { r = 2; mr = mc; }
+  if (md < mr) { r = 3; }
+  return (same && nz) ? r : -1;
+}
+
+// coefficient vectors (over v[0..8] = F_{s-4..s+4}) of the curvatures
+__device__ __forceinline__ void add_curv(double (&w)[9], int centre, double s) {
+  // C_j = F_{j+1} - 2 F_j + F_{j-1}, centre j in window index
+  w[centre - 1] += s;
+  w[centre] -= 2.0 * s;
+  w[centre + 1] += s;
+}
+
+// DM choice k over the pair (Ca at centre ca, Cb at centre cb) with the
+// argument order (4Ca - Cb, 4Cb - Ca, Ca, Cb)
+__device__ __forceinline__ void add_dm(double (&w)[9], int k, int ca, int cb, double s) {
+  switch (k) {
+    case 0: add_curv(w, ca, 4.0 * s); add_curv(w, cb, -s); break;
+    case 1: add_curv(w, cb, 4.0 * s); add_curv(w, ca, -s); break;
+    case 2: add_curv(w, ca, s); break;
+    case 3: add_curv(w, cb, s); break;
+    default: break;
+  }
+}
+
+// Recompute the forward interface value of the window v (same operations and
+// comparisons as mp9_face_fp64 inside the march) and return the coefficients
+// w of the chosen linear expression: Fhat = sum_m w[m] v[m].
+__device__ void mp9_linearize(const double (&v)[9], double (&w)[9]) {
+  using B = Mp9Coef;
+  double d[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) d[k] = v[k + 1] - v[k];
+  double a = B::b0 * d[0];
+  a = fma(B::b1, d[1], a);
+  a = fma(B::b2, d[2], a);
+  a = fma(B::b3, d[3], a);
+  a = fma(B::b4, d[4], a);
+  a = fma(B::b5, d[5], a);
+  a = fma(B::b6, d[6], a);
+  a = fma(B::b7, d[7], a);
+  const double cm1 = d[3] - d[2], c0 = d[4] - d[3], c1 = d[5] - d[4];
+  // DM+ over (C_s, C_{s+1}); DM- as the march carries it: the DM+ of the
+  // previous interface, over (C_{s-1}, C_s)
+  const int kp = minmod4_choice(dbits(fma(4.0, c0, -c1)), dbits(fma(4.0, c1, -c0)), dbits(c0),
+                                dbits(c1));
+  const int km = minmod4_choice(dbits(fma(4.0, cm1, -c0)), dbits(fma(4.0, c0, -cm1)), dbits(cm1),
+                                dbits(c0));
+  const double cand_p[4] = {fma(4.0, c0, -c1), fma(4.0, c1, -c0), c0, c1};
+  const double cand_m[4] = {fma(4.0, cm1, -c0), fma(4.0, c0, -cm1), cm1, c0};
+  const double dmp = kp < 0 ? 0.0 : cand_p[kp];
+  const double dmm = km < 0 ? 0.0 : cand_m[km];
+  // candidate keys (twice their value), as in the forward
+  enum { Z = 0, D0 = 1, MD = 2, UL = 3, LC = 4, A = 5 };
+  long long k[5];
+  k[Z] = 0;
+  k[D0] = key_times_pow2<1>(dbits(d[4]));
+  k[MD] = okey(dbits(d[4] - dmp));
+  k[UL] = key_times_pow2<3>(dbits(d[3]));
+  k[LC] = okey(dbits(fma(8.0 / 3.0, dmm, d[3])));
+  const long long ka = key_times_pow2<1>(dbits(a));
+  // lo = kmax(kmin(0, kmin(k_d0, k_md)), kmin(0, kmin(k_ul, k_lc))), with the
+  // forward's tie rules: kmin(a, b) = a < b ? a : b, kmax(a, b) = a < b ? b : a
+  auto kmin_i = [&](int i, int j) { return k[i] < k[j] ? i : j; };
+  auto kmax_i = [&](int i, int j) { return k[i] < k[j] ? j : i; };
+  const int lo = kmax_i(kmin_i(Z, kmin_i(D0, MD)), kmin_i(Z, kmin_i(UL, LC)));
+  const int hi = kmin_i(kmax_i(Z, kmax_i(D0, MD)), kmax_i(Z, kmax_i(UL, LC)));
+  // r = kmin(kmax(ka, lo), hi)
+  int sel = (ka < k[lo]) ? lo : A;
+  const long long ks = sel == A ? ka : k[sel];
+  if (!(ks < k[hi])) sel = hi;
+#pragma unroll
+  for (int m = 0; m < 9; ++m) w[m] = 0.0;
+  w[4] = 1.0;  // F_s
+  switch (sel) {
+    case A: {
+      const double b[8] = {B::b0, B::b1, B::b2, B::b3, B::b4, B::b5, B::b6, B::b7};
+#pragma unroll
+      for (int m = 0; m < 9; ++m) w[m] += (m > 0 ? b[m - 1] : 0.0) - (m < 8 ? b[m] : 0.0);
+      break;
+    }
+    case D0: w[5] += 1.0; w[4] -= 1.0; break;
+    case MD:  // (d_0 - DM+)/2
+      w[5] += 0.5; w[4] -= 0.5;
+      add_dm(w, kp, 4, 5, -0.5);
+      break;
+    case UL: w[4] += 4.0; w[3] -= 4.0; break;
+    case LC:  // d_-1/2 + (4/3) DM-
+      w[4] += 0.5; w[3] -= 0.5;
+      add_dm(w, km, 3, 4, 4.0 / 3.0);
+      break;
+    default: break;  // Z: F_s
+  }
+}
+
+// ---- equilibrium Jacobian ------------------------------------------------
+
+// Per-cell adjoint of F_eq(mom(R)) given Ebar (adjoint of each equilibrium
+// population): returns the per-population adjoint of R through the moments
+// (rbar_n + rbar_j p + rbar_e p^2 for phi, rbar_e for chi) and the adjoint of
+// D+K at fixed moment sums.  m = (n, j, e) of R.
+template <int QP, int QC>
+struct EqAdj {
+  double rn, rj, re;  // adjoints of the moment sums n, j, e
+  double dk;          // adjoint of D + K
+};
+
+template <int Q>
+__device__ __forceinline__ void axis_g_derivs(const double* wH, double u, double T, double (&g)[Q],
+                                              double (&gu)[Q], double (&gT)[Q]) {
+  double a[Q];
+  a[0] = 1.0;
+  if (Q > 1) a[1] = u;
+  const double tm1 = T - 1.0;
+#pragma unroll
+  for (int l = 2; l < Q; ++l) a[l] = fma(u, a[l - 1], ((double)(l - 1) * tm1) * a[l - 2]);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    double s = 0.0, su = 0.0, sT = 0.0;
+#pragma unroll
+    for (int l = 0; l < Q; ++l) {
+      const double c = wH[l * kMaxQ + k];
+      s = fma(c, a[l], s);
+      if (l >= 1) su = fma(c * (double)l, a[l - 1], su);
+      if (l >= 2) sT = fma(c * (0.5 * l * (l - 1)), a[l - 2], sT);
+    }
+    g[k] = s;
+    gu[k] = su;
+    gT[k] = sT;
+  }
+}
+
+template <int QP, int QC>
+__device__ __forceinline__ EqAdj<QP, QC> eq_adjoint(const DevParams& p, double n, double j,
+                                                    double e, const double* Ebar) {
+  const double inv_n = 1.0 / n;
+  const double u = j * inv_n;
+  const double T = (e - n * u * u) * inv_n * p.invDK;
+  double g[QP], gu[QP], gT[QP];
+  axis_g_derivs<QP>(p.wHp, u, T, g, gu, gT);
+  double h[QC], hu[QC], hT[QC];
+  axis_g_derivs<QC>(p.wHc, u, T, h, hu, hT);
+  double nb = 0.0, ub = 0.0, Tb = 0.0, kb = 0.0;
+#pragma unroll
+  for (int k = 0; k < QP; ++k) {
+    const double eb = Ebar[k];
+    nb = fma(eb, g[k], nb);
+    ub = fma(eb, n * gu[k], ub);
+    Tb = fma(eb, n * gT[k], Tb);
+  }
+  const double kc = p.kchi;
+#pragma unroll
+  for (int q = 0; q < QC; ++q) {
+    const double eb = Ebar[QP + q];
+    nb = fma(eb, kc * T * h[q], nb);
+    ub = fma(eb, kc * T * n * hu[q], ub);
+    Tb = fma(eb, kc * n * (h[q] + T * hT[q]), Tb);
+    kb = fma(eb, T * n * h[q], kb);
+  }
+  // (n, u, T) of (n, j, e): u = j/n, T = (e - j^2/n)/((D+K) n)
+  EqAdj<QP, QC> r;
+  const double DK = p.DK;
+  r.rn = nb - ub * u * inv_n + Tb * (2.0 * n * u * u - e) * inv_n * inv_n / DK;
+  r.rj = ub * inv_n - Tb * 2.0 * u * inv_n / DK;
+  r.re = Tb * inv_n / DK;
+  r.dk = -Tb * T / DK + kb;  // T = (...)/DK and kchi = DK - d
+  return r;
+}
+
+// Equilibrium populations of (n, j, e) (as the forward kernels form them).
+template <int QP, int QC>
+__device__ __forceinline__ void eq_of_moments(const DevParams& p, double n, double j, double e,
+                                              double* Feq) {
+  const double inv_n = 1.0 / n;
+  const double u = j * inv_n;
+  const double T = (e - n * u * u) * inv_n * p.invDK;
+  double g[QP], gu[QP], gT[QP];
+  axis_g_derivs<QP>(p.wHp, u, T, g, gu, gT);
+  double h[QC], hu[QC], hT[QC];
+  axis_g_derivs<QC>(p.wHc, u, T, h, hu, hT);
+#pragma unroll
+  for (int k = 0; k < QP; ++k) Feq[k] = n * g[k];
+  const double nchi = p.kchi * T * n;
+#pragma unroll
+  for (int q = 0; q < QC; ++q) Feq[QP + q] = nchi * h[q];
+}
+
+template <int QP, int QC>
+__device__ __forceinline__ void moments_of(const DevParams& p, const double* F, double& n,
+                                           double& j, double& e) {
+  n = 0.0;
+  j = 0.0;
+  e = 0.0;
+#pragma unroll
+  for (int k = 0; k < QP; ++k) {
+    n += F[k];
+    j = fma(p.px[k], F[k], j);
+    e = fma(p.p2[k], F[k], e);
+  }
+#pragma unroll
+  for (int q = 0; q < QC; ++q) e += F[QP + q];
+}
+
+// ---- the three adjoint stage kernels -------------------------------------
+
+// Shared memory: per population, the contributions of the tile's interfaces
+// to their 9 window cells.
+template <int P>
+struct AdjSmem {
+  double ctr[P][kNI][9];
+  double fbar[P][kTX];
+};
+
+__device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+// Window cell of slot m for interface i (between cells i-1 and i) and sign.
+__device__ __forceinline__ int slot_cell(int i, int m, int sgn) {
+  return sgn > 0 ? (i - 1) + (m - 4) : i - (m - 4);
+}
+
+// dt L^T: the adjoint of X = dt L(Fin) for the tile's cells, every population,
+// into sm.fbar.  Xbar(pop, cell) gives the adjoint of X at any cell.
+template <int QP, int QC, typename XbarFn>
+__device__ __forceinline__ void advect_adjoint(const DevParams& p, const double* Fin, int x0,
+                                               AdjSmem<(QP + QC)>& sm, XbarFn Xbar) {
+  constexpr int P = QP + QC;
+  const int nx = p.nx;
+  const int64_t N = p.N;
+  const int tid = threadIdx.x;
+  for (int t = tid; t < P * kNI; t += kNT) {
+    const int pop = t / kNI;
+    const int ii = t % kNI;
+    const int i = x0 - 5 + ii;  // interface index
+    double* c = sm.ctr[pop][ii];
+    if (i < 0 || i > nx) {
+#pragma unroll
+      for (int m = 0; m < 9; ++m) c[m] = 0.0;
+      continue;
+    }
+    const double px = p.px[pop];
+    const int sgn = px >= 0.0 ? 1 : -1;
+    double v[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) v[m] = Fin[pop * N + clampi(slot_cell(i, m, sgn), nx)];
+    double w[9];
+    mp9_linearize(v, w);
+    // X_c = (dt p / dx) (Fhat_{c+1} - Fhat_c): Fhat_i enters X_{i-1} with +, X_i with -
+    const double cp = p.dtdx * px;
+    const double xl = (i - 1 >= 0) ? Xbar(pop, i - 1) : 0.0;
+    const double xr = (i <= nx - 1) ? Xbar(pop, i) : 0.0;
+    const double fb = cp * (xl - xr);
+#pragma unroll
+    for (int m = 0; m < 9; ++m) c[m] = fb * w[m];
+  }
+  __syncthreads();
+  for (int t = tid; t < P * kTX; t += kNT) {
+    const int pop = t / kTX;
+    const int lc = t % kTX;
+    const int cell = x0 + lc;
+    double acc = 0.0;
+    if (cell < nx) {
+      const int sgn = p.px[pop] >= 0.0 ? 1 : -1;
+      for (int ii = 0; ii < kNI; ++ii) {
+        const int i = x0 - 5 + ii;
+        if (i < 0 || i > nx) continue;
+#pragma unroll
+        for (int m = 0; m < 9; ++m)
+          if (clampi(slot_cell(i, m, sgn), nx) == cell) acc += sm.ctr[pop][ii][m];
+      }
+    }
+    sm.fbar[pop][lc] = acc;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void block_add(double* dst, double v) {
+  // warp sum then one atomic per warp
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(dst, v);
+}
+
+// Stage 4 + final: from Gbar = adjoint of F^{n+1}.
+template <int QP, int QC>
+__global__ void __launch_bounds__(kNT) adj4_kernel(const __grid_constant__ DevParams p,
+                                                   const __grid_constant__ AdjParams a) {
+  constexpr int P = QP + QC;
+  __shared__ AdjSmem<P> sm;
+  const StageCoef& sc = p.sc;
+  const int x0 = blockIdx.x * kTX;
+  const int64_t N = p.N;
+  // X4bar = -wt4 Gbar
+  advect_adjoint<QP, QC>(p, a.F4s, x0, sm,
+                         [&](int pop, int c) { return -sc.wt4 * a.Gbar[pop * N + c]; });
+  const int lc = threadIdx.x;
+  const int cell = x0 + lc;
+  double s_a44 = 0.0, s_w4 = 0.0, s_dk = 0.0;
+  if (lc < kTX && cell < p.nx) {
+    double F4[P], Eb[P], G[P], F4b[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      F4[k] = a.F4s[k * N + cell];
+      G[k] = a.Gbar[k * N + cell];
+      F4b[k] = sm.fbar[k][lc];
+    }
+    double n, j, e;
+    moments_of<QP, QC>(p, F4, n, j, e);  // moments of F4 = moments of R4
+    double E4[P];
+    eq_of_moments<QP, QC>(p, n, j, e, E4);
+    const double inv = 1.0 / (1.0 - sc.a44e4);
+    double R4b[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const double D4 = (F4[k] - E4[k]) * inv;  // R4 - E4
+      R4b[k] = (1.0 - sc.a44e4) * F4b[k] - sc.w4e4 * G[k];
+      Eb[k] = sc.a44e4 * F4b[k] + sc.w4e4 * G[k];
+      s_a44 -= F4b[k] * D4;
+      s_w4 -= G[k] * D4;
+    }
+    const EqAdj<QP, QC> ea = eq_adjoint<QP, QC>(p, n, j, e, Eb);
+    s_dk = ea.dk;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      double rb = R4b[k] + (k < QP ? fma(p.p2[k], ea.re, fma(p.px[k], ea.rj, ea.rn)) : ea.re);
+      a.A4bar[k * N + cell] = rb;
+      a.X3bar[k * N + cell] = -sc.wt3 * G[k] - sc.at43 * rb;
+    }
+  }
+  block_add(&a.scal[kBarA44e4], s_a44);
+  block_add(&a.scal[kBarW4e4], s_w4);
+  block_add(&a.scal[kBarDK], s_dk);
+}
+
+// Stage 3.
+template <int QP, int QC>
+__global__ void __launch_bounds__(kNT) adj3_kernel(const __grid_constant__ DevParams p,
+                                                   const __grid_constant__ AdjParams a) {
+  constexpr int P = QP + QC;
+  __shared__ AdjSmem<P> sm;
+  const StageCoef& sc = p.sc;
+  const int x0 = blockIdx.x * kTX;
+  const int64_t N = p.N;
+  advect_adjoint<QP, QC>(p, a.F3s, x0, sm, [&](int pop, int c) { return a.X3bar[pop * N + c]; });
+  const int lc = threadIdx.x;
+  const int cell = x0 + lc;
+  double s[7] = {0, 0, 0, 0, 0, 0, 0};  // a33e3 a43e3 w3e3 k3 k4 kf dk
+  if (lc < kTX && cell < p.nx) {
+    double F3[P], Fn[P], G[P], A4b[P], F3b[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      F3[k] = a.F3s[k * N + cell];
+      Fn[k] = a.Fn[k * N + cell];
+      G[k] = a.Gbar[k * N + cell];
+      A4b[k] = a.A4bar[k * N + cell];
+      F3b[k] = sm.fbar[k][lc];
+    }
+    double n, j, e, n0, j0, e0;
+    moments_of<QP, QC>(p, F3, n, j, e);
+    moments_of<QP, QC>(p, Fn, n0, j0, e0);
+    double E3[P], E0[P];
+    eq_of_moments<QP, QC>(p, n, j, e, E3);
+    eq_of_moments<QP, QC>(p, n0, j0, e0, E0);
+    const double inv = 1.0 / (1.0 - sc.a33e3);
+    double R3b[P], Eb[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const double D3 = (F3[k] - E3[k]) * inv;
+      R3b[k] = (1.0 - sc.a33e3) * F3b[k] - sc.a43e3 * A4b[k] - sc.w3e3 * G[k];
+      Eb[k] = sc.a33e3 * F3b[k] + sc.a43e3 * A4b[k] + sc.w3e3 * G[k];
+      s[0] -= F3b[k] * D3;
+      s[1] -= A4b[k] * D3;
+      s[2] -= G[k] * D3;
+    }
+    const EqAdj<QP, QC> ea = eq_adjoint<QP, QC>(p, n, j, e, Eb);
+    s[6] = ea.dk;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const double rb = R3b[k] + (k < QP ? fma(p.p2[k], ea.re, fma(p.px[k], ea.rj, ea.rn)) : ea.re);
+      const double D = Fn[k] - E0[k];
+      s[3] -= rb * D;
+      s[4] -= A4b[k] * D;
+      s[5] -= G[k] * D;
+      a.Fpart[k * N + cell] = rb + A4b[k] + G[k];
+      a.Dbar[k * N + cell] = -sc.k3 * rb - sc.k4 * A4b[k] - sc.kf * G[k];
+      a.X2bar[k * N + cell] = -sc.at32 * rb - sc.at42 * A4b[k] - sc.wt2 * G[k];
+    }
+  }
+  block_add(&a.scal[kBarA33e3], s[0]);
+  block_add(&a.scal[kBarA43e3], s[1]);
+  block_add(&a.scal[kBarW3e3], s[2]);
+  block_add(&a.scal[kBarK3], s[3]);
+  block_add(&a.scal[kBarK4], s[4]);
+  block_add(&a.scal[kBarKf], s[5]);
+  block_add(&a.scal[kBarDK], s[6]);
+}
+
+// Stage 2 (and the stage-1/2 closed forms): adjoint of F^n.
+template <int QP, int QC>
+__global__ void __launch_bounds__(kNT) adj2_kernel(const __grid_constant__ DevParams p,
+                                                   const __grid_constant__ AdjParams a) {
+  constexpr int P = QP + QC;
+  __shared__ AdjSmem<P> sm;
+  const StageCoef& sc = p.sc;
+  const int x0 = blockIdx.x * kTX;
+  const int64_t N = p.N;
+  advect_adjoint<QP, QC>(p, a.F2s, x0, sm, [&](int pop, int c) { return a.X2bar[pop * N + c]; });
+  const int lc = threadIdx.x;
+  const int cell = x0 + lc;
+  double s_c2 = 0.0, s_dk = 0.0;
+  if (lc < kTX && cell < p.nx) {
+    double Fn[P], F2b[P], Eb[P], Dt[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      Fn[k] = a.Fn[k * N + cell];
+      F2b[k] = sm.fbar[k][lc];
+    }
+    double n0, j0, e0;
+    moments_of<QP, QC>(p, Fn, n0, j0, e0);
+    double E0[P];
+    eq_of_moments<QP, QC>(p, n0, j0, e0, E0);
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      Dt[k] = a.Dbar[k * N + cell] + sc.c2 * F2b[k];  // total adjoint of D
+      Eb[k] = F2b[k] - Dt[k];                          // F2 = E0 + c2 D, D = F - E0
+      s_c2 += F2b[k] * (Fn[k] - E0[k]);
+    }
+    const EqAdj<QP, QC> ea = eq_adjoint<QP, QC>(p, n0, j0, e0, Eb);
+    s_dk = ea.dk;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const double rb = k < QP ? fma(p.p2[k], ea.re, fma(p.px[k], ea.rj, ea.rn)) : ea.re;
+      a.Gnew[k * N + cell] = a.Fpart[k * N + cell] + Dt[k] + rb;
+    }
+  }
+  block_add(&a.scal[kBarC2], s_c2);
+  block_add(&a.scal[kBarDK], s_dk);
+}
+
+// ---- initial fields and their adjoint ---------------------------------------
+
+template <int QP, int QC>
+__global__ void init_fields_kernel(const __grid_constant__ DevParams p, const double* __restrict__ n,
+                                   const double* __restrict__ u, const double* __restrict__ T) {
+  constexpr int P = QP + QC;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const double nn = n[c], uu = u[c], TT = T[c];
+  // moment sums of the equilibrium of (n, u, T): j = n u, e = n u^2 + (D+K) n T
+  double Feq[P];
+  double g[QP], gu[QP], gT[QP];
+  axis_g_derivs<QP>(p.wHp, uu, TT, g, gu, gT);
+  double h[QC], hu[QC], hT[QC];
+  axis_g_derivs<QC>(p.wHc, uu, TT, h, hu, hT);
+#pragma unroll
+  for (int k = 0; k < QP; ++k) Feq[k] = nn * g[k];
+#pragma unroll
+  for (int q = 0; q < QC; ++q) Feq[QP + q] = p.kchi * TT * nn * h[q];
+  double* F = (double*)p.F;
+#pragma unroll
+  for (int k = 0; k < P; ++k) F[k * p.N + c] = Feq[k];
+}
+
+template <int QP, int QC>
+__global__ void init_fields_adjoint_kernel(const __grid_constant__ DevParams p,
+                                           const double* __restrict__ Fbar,
+                                           const double* __restrict__ n,
+                                           const double* __restrict__ u,
+                                           const double* __restrict__ T, double* __restrict__ nb,
+                                           double* __restrict__ ub, double* __restrict__ Tb,
+                                           double* __restrict__ dkbar) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double s_dk = 0.0;
+  if (c < p.N) {
+    const double nn = n[c], uu = u[c], TT = T[c];
+    double g[QP], gu[QP], gT[QP];
+    axis_g_derivs<QP>(p.wHp, uu, TT, g, gu, gT);
+    double h[QC], hu[QC], hT[QC];
+    axis_g_derivs<QC>(p.wHc, uu, TT, h, hu, hT);
+    double sn = 0.0, su = 0.0, sT = 0.0;
+#pragma unroll
+    for (int k = 0; k < QP; ++k) {
+      const double fb = Fbar[k * p.N + c];
+      sn = fma(fb, g[k], sn);
+      su = fma(fb, nn * gu[k], su);
+      sT = fma(fb, nn * gT[k], sT);
+    }
+#pragma unroll
+    for (int q = 0; q < QC; ++q) {
+      const double fb = Fbar[(QP + q) * p.N + c];
+      sn = fma(fb, p.kchi * TT * h[q], sn);
+      su = fma(fb, p.kchi * TT * nn * hu[q], su);
+      sT = fma(fb, p.kchi * nn * (h[q] + TT * hT[q]), sT);
+      s_dk = fma(fb, TT * nn * h[q], s_dk);  // chi^eq = (D+K-d) T n h
+    }
+    nb[c] = sn;
+    ub[c] = su;
+    Tb[c] = sT;
+  }
+  block_add(dkbar, s_dk);
+}
+
+}  // namespace
+}  // namespace fdlb
+
+// ---- host side ------------------------------------------------------------------
+
+namespace {
+
+using fdlb::DevParams;
+
+bool adjoint_lattice(const fdlb_ctx* c) {
+  return !c->batch && !c->custom_tableau && c->dp.d == 1 && c->precision == FDLB_FP64 &&
+         ((c->dp.Qp == 8 && c->dp.Qc == 8) || (c->dp.Qp == 5 && c->dp.Qc == 3) ||
+          (c->dp.Qp == 3 && c->dp.Qc == 3)) &&
+         c->dp.bc == FDLB_BC_OUTLET;
+}
+
+template <int QP, int QC>
+int launch_adj(int which, const DevParams& p, const fdlb::AdjParams& a, cudaStream_t s) {
+  const int nb = (p.nx + fdlb::kTX - 1) / fdlb::kTX;
+  if (which == 4) fdlb::adj4_kernel<QP, QC><<<nb, fdlb::kNT, 0, s>>>(p, a);
+  else if (which == 3) fdlb::adj3_kernel<QP, QC><<<nb, fdlb::kNT, 0, s>>>(p, a);
+  else fdlb::adj2_kernel<QP, QC><<<nb, fdlb::kNT, 0, s>>>(p, a);
+  return (int)cudaGetLastError();
+}
+
+int launch_adj_any(int which, const DevParams& p, const fdlb::AdjParams& a, cudaStream_t s) {
+  if (p.Qp == 8) return launch_adj<8, 8>(which, p, a, s);
+  if (p.Qp == 5) return launch_adj<5, 3>(which, p, a, s);
+  return launch_adj<3, 3>(which, p, a, s);
+}
+
+// Derivatives of the fused stage coefficients with respect to lam = dt/tau,
+// for the paper's tableau (the only one the adjoint supports).
+void stage_coef_dlam(double lam, double* dc) {
+  const double al = 0.24169426078821, be = 0.06042356519705, et = 0.12915286960590;
+  const double A[4][4] = {{al, 0, 0, 0}, {-al, al, 0, 0}, {0, 1 - al, al, 0},
+                          {be, et, 0.5 - be - et - al, al}};
+  const double w[4] = {0.0, 1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+  double e[4], de[4];
+  for (int i = 0; i < 4; ++i) {
+    const double den = 1.0 + A[i][i] * lam;
+    e[i] = lam / den;
+    de[i] = 1.0 / (den * den);
+  }
+  const double d1 = e[0], dd1 = de[0];
+  const double d2 = e[1] * (1.0 - A[1][0] * d1);
+  const double dd2 = de[1] * (1.0 - A[1][0] * d1) - e[1] * A[1][0] * dd1;
+  (void)d2;
+  dc[fdlb::kBarC2] = -A[1][0] * dd1 - A[1][1] * dd2;
+  dc[fdlb::kBarK3] = A[2][0] * dd1 + A[2][1] * dd2;
+  dc[fdlb::kBarK4] = A[3][0] * dd1 + A[3][1] * dd2;
+  dc[fdlb::kBarKf] = w[0] * dd1 + w[1] * dd2;
+  dc[fdlb::kBarA33e3] = A[2][2] * de[2];
+  dc[fdlb::kBarA43e3] = A[3][2] * de[2];
+  dc[fdlb::kBarW3e3] = w[2] * de[2];
+  dc[fdlb::kBarA44e4] = A[3][3] * de[3];
+  dc[fdlb::kBarW4e4] = w[3] * de[3];
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdlb_init_fields(fdlb_ctx* c, const double* n, const double* u, const double* T) {
+  if (!c || !n || !u || !T) return fdlb::ctx_error(c, FDLB_EINVAL, "NULL argument");
+  if (!adjoint_lattice(c))
+    return fdlb::ctx_error(c, FDLB_EINVAL, "fdlb_init_fields: 1-D binary64 outlet contexts");
+  const int nt = 128;
+  const int64_t nb = (c->dp.N + nt - 1) / nt;
+  if (c->dp.Qp == 8) fdlb::init_fields_kernel<8, 8><<<(unsigned)nb, nt, 0, c->stream>>>(c->dp, n, u, T);
+  else if (c->dp.Qp == 5) fdlb::init_fields_kernel<5, 3><<<(unsigned)nb, nt, 0, c->stream>>>(c->dp, n, u, T);
+  else fdlb::init_fields_kernel<3, 3><<<(unsigned)nb, nt, 0, c->stream>>>(c->dp, n, u, T);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fdlb::ctx_error(c, FDLB_ECUDA, cudaGetErrorString(e));
+  c->prepared = false;
+  return fdlb::ctx_prepare(c);
+}
+
+int fdlb_init_fields_adjoint(fdlb_ctx* c, const double* Fbar, const double* n, const double* u,
+                             const double* T, double* nbar, double* ubar, double* Tbar,
+                             double* dgamma) {
+  if (!c || !Fbar || !n || !u || !T || !nbar || !ubar || !Tbar || !dgamma)
+    return fdlb::ctx_error(c, FDLB_EINVAL, "NULL argument");
+  if (!adjoint_lattice(c))
+    return fdlb::ctx_error(c, FDLB_EINVAL, "fdlb_init_fields_adjoint: 1-D binary64 outlet contexts");
+  double* dk = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&dk, sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dk, 0, sizeof(double), c->stream);
+  if (e != cudaSuccess) return fdlb::ctx_error(c, FDLB_ECUDA, cudaGetErrorString(e));
+  const int nt = 128;
+  const int64_t nb = (c->dp.N + nt - 1) / nt;
+  if (c->dp.Qp == 8)
+    fdlb::init_fields_adjoint_kernel<8, 8><<<(unsigned)nb, nt, 0, c->stream>>>(c->dp, Fbar, n, u, T, nbar, ubar, Tbar, dk);
+  else if (c->dp.Qp == 5)
+    fdlb::init_fields_adjoint_kernel<5, 3><<<(unsigned)nb, nt, 0, c->stream>>>(c->dp, Fbar, n, u, T, nbar, ubar, Tbar, dk);
+  else
+    fdlb::init_fields_adjoint_kernel<3, 3><<<(unsigned)nb, nt, 0, c->stream>>>(c->dp, Fbar, n, u, T, nbar, ubar, Tbar, dk);
+  double h = 0.0;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dk, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(dk, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fdlb::ctx_error(c, FDLB_ECUDA, cudaGetErrorString(e));
+  const double g = c->gamma;
+  *dgamma = h * (-2.0 / ((g - 1.0) * (g - 1.0)));  // D + K = 2/(gamma - 1)
+  return FDLB_OK;
+}
+
+int fdlb_forward_ckpt(fdlb_ctx* c, int64_t nsteps, int every, void* ckpt) {
+  if (!c || !ckpt || nsteps < 0 || every < 1) return fdlb::ctx_error(c, FDLB_EINVAL, "bad arguments");
+  if (!adjoint_lattice(c))
+    return fdlb::ctx_error(c, FDLB_EINVAL, "checkpointed runs: 1-D binary64 outlet contexts");
+  int rc = fdlb::ctx_prepare(c);
+  if (rc) return rc;
+  const size_t bytes = fdlb_state_bytes(c);
+  char* ck = (char*)ckpt;
+  cudaError_t e = cudaSuccess;
+  for (int64_t s = 0; s <= nsteps && e == cudaSuccess; ++s) {
+    if (s % every == 0)
+      e = cudaMemcpyAsync(ck + (s / every) * bytes, c->dp.F, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (s == nsteps || e != cudaSuccess) break;
+    for (int st : {fdlb::kStage3, fdlb::kStage4, fdlb::kFinal}) {
+      int le = fdlb::ctx_launch_stage(c, st, c->stream);
+      if (le) {
+        e = (cudaError_t)le;
+        break;
+      }
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->status_host, c->dp.status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return fdlb::ctx_error(c, FDLB_ECUDA, cudaGetErrorString(e));
+  if (*c->status_host & 1u)
+    return fdlb::ctx_error(c, FDLB_EUNSTABLE, "a cell reached n <= 0, T <= 0 or a non-finite moment");
+  return FDLB_OK;
+}
+
+int fdlb_adjoint(fdlb_ctx* c, int64_t nsteps, int every, const void* ckpt, double* Fbar,
+                 double* dparams) {
+  if (!c || !ckpt || !Fbar || !dparams || nsteps < 0 || every < 1)
+    return fdlb::ctx_error(c, FDLB_EINVAL, "bad arguments");
+  if (!adjoint_lattice(c))
+    return fdlb::ctx_error(c, FDLB_EINVAL, "the adjoint covers 1-D binary64 outlet contexts");
+  const size_t bytes = fdlb_state_bytes(c);
+  // work space: per step of a segment the saved F^n, F2, F3 and F4 (one more
+  // slot for the state after the segment's last step), 5 adjoint arrays and
+  // the scalar accumulators
+  const size_t need = (size_t)(4 * every + 4 + 5) * bytes + 256;
+  if (c->adj_bytes < need) {
+    if (c->adj_buf) cudaFree(c->adj_buf);
+    c->adj_buf = nullptr;
+    c->adj_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->adj_buf, need);
+    if (e != cudaSuccess) return fdlb::ctx_error(c, FDLB_ENOMEM, "adjoint work space");
+    c->adj_bytes = need;
+  }
+  char* w = (char*)c->adj_buf;
+  auto slot = [&](int64_t k, int which) { return (double*)(w + ((size_t)k * 4 + which) * bytes); };
+  double* A4b = slot(every + 1, 0);
+  double* X3b = A4b + bytes / 8;
+  double* X2b = X3b + bytes / 8;
+  double* Fpt = X2b + bytes / 8;
+  double* Db = Fpt + bytes / 8;
+  double* scal = Db + bytes / 8;
+  cudaStream_t s = c->stream;
+  cudaError_t e = cudaMemsetAsync(scal, 0, fdlb::kNumAdjScalars * sizeof(double), s);
+  const int64_t nseg = (nsteps + every - 1) / every;
+  for (int64_t sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
+    const int64_t s0 = sg * every;
+    const int64_t ns = (nsteps - s0 < every) ? nsteps - s0 : every;
+    // recompute the segment from its checkpoint: every launch gets its own
+    // array pointers, so the stage kernels leave F^n, F2, F3 and F4 of each
+    // step in its slot (the final stage writes F^{n+1} and its F2 into the
+    // next slot); D and Af are the context's own scratch arrays
+    e = cudaMemcpyAsync(slot(0, 0), (const char*)ckpt + sg * bytes, bytes,
+                        cudaMemcpyDeviceToDevice, s);
+    int le = 0;
+    if (e == cudaSuccess) {
+      DevParams q = c->dp;
+      q.F = slot(0, 0);
+      q.F2 = slot(0, 1);
+      le = fdlb::launch_stage(q, fdlb::kPrep, s);
+    }
+    for (int64_t k = 0; k < ns && e == cudaSuccess && !le; ++k) {
+      DevParams q = c->dp;
+      q.F = slot(k, 0);
+      q.F2 = slot(k, 1);
+      q.F3 = slot(k, 2);
+      q.A4 = slot(k, 3);
+      le = fdlb::launch_stage(q, fdlb::kStage3, s);
+      if (!le) le = fdlb::launch_stage(q, fdlb::kStage4, s);
+      q.F = slot(k + 1, 0);
+      q.F2 = slot(k + 1, 1);
+      if (!le) le = fdlb::launch_stage(q, fdlb::kFinal, s);
+    }
+    if (le) e = (cudaError_t)le;
+    // adjoint steps of the segment, last step first; Fbar is updated in
+    // place (the stage-2 adjoint reads no adjoint of F^{n+1})
+    for (int64_t k = ns - 1; k >= 0 && e == cudaSuccess; --k) {
+      fdlb::AdjParams a{};
+      a.Fn = slot(k, 0);
+      a.F2s = slot(k, 1);
+      a.F3s = slot(k, 2);
+      a.F4s = slot(k, 3);
+      a.Gbar = Fbar;
+      a.A4bar = A4b;
+      a.X3bar = X3b;
+      a.X2bar = X2b;
+      a.Fpart = Fpt;
+      a.Dbar = Db;
+      a.Gnew = Fbar;
+      a.scal = scal;
+      int r = launch_adj_any(4, c->dp, a, s);
+      if (!r) r = launch_adj_any(3, c->dp, a, s);
+      if (!r) r = launch_adj_any(2, c->dp, a, s);
+      if (r) e = (cudaError_t)r;
+    }
+  }
+  double h[fdlb::kNumAdjScalars] = {0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, scal, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fdlb::ctx_error(c, FDLB_ECUDA, cudaGetErrorString(e));
+  // the context's D and Af scratch arrays were overwritten: derive them anew
+  c->prepared = false;
+  // d/dgamma through D + K = 2/(gamma - 1); d/dtau through lam = dt/tau
+  const double g = c->gamma;
+  dparams[0] = h[fdlb::kBarDK] * (-2.0 / ((g - 1.0) * (g - 1.0)));
+  const double lam = c->dt / c->tau;
+  double dc[fdlb::kNumAdjScalars] = {0};
+  stage_coef_dlam(lam, dc);
+  double dlam = 0.0;
+  for (int i = 0; i < fdlb::kBarDK; ++i) dlam += h[i] * dc[i];
+  dparams[1] = dlam * (-lam / c->tau);
+  return fdlb::ctx_prepare(c);
+}
+
+}  // extern "C"

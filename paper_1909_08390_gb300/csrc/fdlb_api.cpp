@@ -13,34 +13,12 @@
 #include <algorithm>
 
 #include "fdlb.h"
+#include "fdlb_ctx.h"
 #include "fdlb_internal.h"
 
 using fdlb::DevParams;
 using fdlb::kMaxQ;
 
-struct fdlb_ctx {
-  DevParams dp{};
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  int precision = FDLB_FP64;
-  fdlb_grid grid{};
-  double gamma = 0, tau = 0, dt = 0;
-  void* buf = nullptr;  // one allocation: 6 population arrays, 4 moment fields, status
-  double* mom = nullptr;  // device moments buffer (n, ux, uy, T) for host copies
-  size_t buf_bytes = 0;
-  unsigned* status_host = nullptr;  // pinned
-  bool prepared = false;
-  std::string err;
-  // batches of 1-D problems (fdlb_create_batch)
-  bool batch = false;
-  std::vector<fdlb::BatchProblem> probs;
-  fdlb::BatchProblem* probs_dev = nullptr;
-  fdlb::WorkItem* work_dev = nullptr;
-  int nsm = 0;
-  // CUDA graph of kGraphSteps steps, captured on first use
-  cudaStream_t capture_stream = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
-};
 
 namespace {
 
@@ -357,6 +335,11 @@ int params_for(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double t
 // Record a context-less error for fdlb_last_error(NULL).
 int record_error(int code, const char* msg) { return set_err(nullptr, code, "%s", msg); }
 
+// Error recording, preparation and stage launch for the other host files.
+int ctx_error(fdlb_ctx* c, int code, const char* msg) { return set_err(c, code, "%s", msg); }
+int ctx_prepare(fdlb_ctx* c) { return ensure_prepared(c); }
+int ctx_launch_stage(fdlb_ctx* c, int stage, cudaStream_t s) { return launch_stage_any(c, stage, s); }
+
 }  // namespace fdlb
 
 extern "C" {
@@ -400,6 +383,7 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
   if (!c) return set_err(nullptr, FDLB_ENOMEM, "host allocation failed");
   c->grid = g;
   c->grid.ny = ny;
+  c->custom_tableau = tableau != nullptr;
   c->gamma = gamma;
   c->tau = tau;
   c->dt = dt;
@@ -925,6 +909,7 @@ void fdlb_destroy(fdlb_ctx* c) {
   if (c->probs_dev) cudaFree(c->probs_dev);
   if (c->work_dev) cudaFree(c->work_dev);
   if (c->buf) cudaFree(c->buf);
+  if (c->adj_buf) cudaFree(c->adj_buf);
   if (c->status_host) cudaFreeHost(c->status_host);
   delete c;
 }

@@ -96,6 +96,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fdlb_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int)]
     lib.fdlb_batch_set_tiling.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    lib.fdlb_init_fields.argtypes = [_vp, _vp, _vp, _vp]
+    lib.fdlb_init_fields_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _dp]
+    lib.fdlb_forward_ckpt.argtypes = [_vp, ctypes.c_int64, ctypes.c_int, _vp]
+    lib.fdlb_adjoint.argtypes = [_vp, ctypes.c_int64, ctypes.c_int, _vp, _vp, _dp]
     lib.fdlb_step_noalloc.argtypes = [ctypes.POINTER(fdlb_grid), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.POINTER(fdlb_tableau), _vp, ctypes.c_int64, _vp]
@@ -262,6 +266,31 @@ def fdlb_batch_set_tiling(ctx, variant: int, ctas_per_sm: int):
     _check(load().fdlb_batch_set_tiling(ctx, int(variant), int(ctas_per_sm)), ctx)
 
 
+def fdlb_init_fields(ctx, n, u, T):
+    """F = equilibrium of the per-cell fields (torch CUDA float64 tensors)."""
+    _check(load().fdlb_init_fields(ctx, n.data_ptr(), u.data_ptr(), T.data_ptr()), ctx)
+
+
+def fdlb_init_fields_adjoint(ctx, Fbar, n, u, T, nbar, ubar, Tbar) -> float:
+    dg = ctypes.c_double(0.0)
+    _check(load().fdlb_init_fields_adjoint(ctx, Fbar.data_ptr(), n.data_ptr(), u.data_ptr(),
+                                           T.data_ptr(), nbar.data_ptr(), ubar.data_ptr(),
+                                           Tbar.data_ptr(), ctypes.byref(dg)), ctx)
+    return dg.value
+
+
+def fdlb_forward_ckpt(ctx, nsteps: int, every: int, ckpt):
+    _check(load().fdlb_forward_ckpt(ctx, int(nsteps), int(every), ckpt.data_ptr()), ctx)
+
+
+def fdlb_adjoint(ctx, nsteps: int, every: int, ckpt, Fbar):
+    """Fbar (in: dL/dF(nsteps), out: dL/dF(0)); returns (dL/dgamma, dL/dtau) of the steps."""
+    d = (ctypes.c_double * 2)()
+    _check(load().fdlb_adjoint(ctx, int(nsteps), int(every), ckpt.data_ptr(), Fbar.data_ptr(), d),
+           ctx)
+    return d[0], d[1]
+
+
 def fdlb_destroy(ctx):
     if ctx:
         load().fdlb_destroy(ctx)
@@ -397,3 +426,112 @@ class BatchSolver(Solver):
     def member(self, arr, i):
         """Slice of problem i from a concatenated per-cell array (last axis)."""
         return arr[..., self.base[i]:self.base[i] + self.nxs[i]]
+
+
+# ---- differentiation (torch.autograd) --------------------------------------
+
+def _field_context(spec, gamma: float, tau: float, n0, u0, T0):
+    """A 1-D binary64 outlet context whose state is the equilibrium of the
+    fields (n0, u0, T0) (CUDA float64 tensors of spec['nx'] cells)."""
+    import torch
+    Q = spec["Q"]
+    Qphi, Qchi = Q if isinstance(Q, tuple) else (Q, Q)
+    g = fdlb_grid(1, spec["nx"], 1, spec["x0"], spec["x1"], 0.0, 1.0, FDLB_BC_OUTLET)
+    ctx = fdlb_create(g, Qphi, Qchi, float(gamma), float(tau), spec["dt"], None, FDLB_FP64,
+                      torch.cuda.current_stream())
+    try:
+        fdlb_init_fields(ctx, *(t.detach().to(torch.float64).contiguous() for t in (n0, u0, T0)))
+    except Exception:
+        fdlb_destroy(ctx)
+        raise
+    return ctx, Qphi
+
+
+def density_forward(n0, u0, T0, gamma, tau, spec):
+    """Final density after spec['nsteps'] steps from the equilibrium of the
+    fields (no gradient; the plain fdlb_step path)."""
+    import torch
+    ctx, Qphi = _field_context(spec, gamma, tau, n0, u0, T0)
+    try:
+        fdlb_step(ctx, spec["nsteps"])
+        FN = torch.empty((fdlb_npop(ctx), spec["nx"]), dtype=torch.float64, device=n0.device)
+        fdlb_get_state(ctx, FN, True)
+        torch.cuda.current_stream().synchronize()
+    finally:
+        fdlb_destroy(ctx)
+    return FN[:Qphi].sum(0)
+
+
+def _autograd_function():
+    import torch
+
+    class DensityRun(torch.autograd.Function):
+        """Final density n(x) after nsteps IMEX steps of a 1-D binary64 problem
+        started from the equilibrium of the fields (n0, u0, T0), as a
+        differentiable function of the fields, gamma and tau.  Forward: the
+        checkpointed run (fdlb_forward_ckpt, a state kept every `every`
+        steps).  Backward: the library's hand-written discrete adjoint
+        (fdlb_adjoint, then fdlb_init_fields_adjoint)."""
+
+        @staticmethod
+        def forward(fctx, n0, u0, T0, gamma, tau, spec):
+            nsteps, every = spec["nsteps"], spec["every"]
+            ctx, Qphi = _field_context(spec, gamma, tau, n0, u0, T0)
+            try:
+                P = fdlb_npop(ctx)
+                ckpt = torch.empty((nsteps // every + 1, P, spec["nx"]), dtype=torch.float64,
+                                   device=n0.device)
+                fdlb_forward_ckpt(ctx, nsteps, every, ckpt)
+                FN = torch.empty((P, spec["nx"]), dtype=torch.float64, device=n0.device)
+                fdlb_get_state(ctx, FN, True)
+                torch.cuda.current_stream().synchronize()
+            finally:
+                fdlb_destroy(ctx)
+            fctx.ckpt, fctx.spec, fctx.Qphi, fctx.P = ckpt, spec, Qphi, P
+            fctx.gamma, fctx.tau = float(gamma), float(tau)
+            fctx.save_for_backward(*(t.detach().to(torch.float64).contiguous() for t in (n0, u0, T0)))
+            return FN[:Qphi].sum(0)  # n = sum of the phi populations (Eq. Moments_discrete)
+
+        @staticmethod
+        def backward(fctx, nbar):
+            n0, u0, T0 = fctx.saved_tensors
+            spec = fctx.spec
+            Fbar = torch.zeros((fctx.P, spec["nx"]), dtype=torch.float64, device=nbar.device)
+            Fbar[:fctx.Qphi] = nbar.to(torch.float64)
+            ctx, _ = _field_context(spec, fctx.gamma, fctx.tau, n0, u0, T0)
+            try:
+                dg, dtau = fdlb_adjoint(ctx, spec["nsteps"], spec["every"], fctx.ckpt, Fbar)
+                nb, ub, Tb = (torch.empty_like(n0) for _ in range(3))
+                dg0 = fdlb_init_fields_adjoint(ctx, Fbar, n0, u0, T0, nb, ub, Tb)
+                torch.cuda.current_stream().synchronize()
+            finally:
+                fdlb_destroy(ctx)
+            fctx.ckpt = None
+            dev = nbar.device
+            return (nb, ub, Tb, torch.tensor(dg + dg0, dtype=torch.float64, device=dev),
+                    torch.tensor(dtau, dtype=torch.float64, device=dev), None)
+
+    return DensityRun
+
+
+_DensityRun = None
+
+
+def density_run(n0, u0, T0, gamma, tau, spec):
+    """Differentiable final density (see DensityRun); spec holds nx, x0, x1,
+    Q (int or (Qphi, Qchi)), dt, nsteps and every."""
+    global _DensityRun
+    if _DensityRun is None:
+        _DensityRun = _autograd_function()
+    return _DensityRun.apply(n0, u0, T0, gamma, tau, spec)
+
+
+def blended_fields(params, nx: int, x0: float = -0.5, x1: float = 0.5, width: float = 0.05):
+    """Initial fields (n, u, T = P/rho) of the blended two-state data (the
+    seeded-input recipe of workloads.blend_states) as differentiable torch
+    operations on params = (rhoL, uL, PL, rhoR, uR, PR)."""
+    import torch
+    from .workloads import blend_states, cell_centres
+    x = torch.as_tensor(cell_centres(nx, x0, x1), dtype=torch.float64, device=params.device)
+    rho, u, P = blend_states(params, x, width, torch.tanh)
+    return rho, u, P / rho

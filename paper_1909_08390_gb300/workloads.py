@@ -15,6 +15,10 @@ Workloads (all inputs synthetic; the paper uses no dataset):
 * ``lax_liu_2d``: the paper's configurations 11 and 12 of the 2-D Riemann
   problem (Sec. V).
 * ``batched_1d``: independent two-state problems of uneven length and gamma.
+* ``adjoint_1d``: the shock-tube states joined by a smooth tanh blend of
+  width 0.05 (so that the run is differentiable), Nx = 2048, Q = 8,
+  gamma = 7/5, tau = 1e-5, dt = 2e-5, 2000 steps, checkpoints every 50
+  steps; the loss compares the final density with a seeded smooth target.
 """
 from __future__ import annotations
 
@@ -182,3 +186,63 @@ def smooth_random_populations(shape, seed: int = 0, amp: float = 0.2) -> np.ndar
             f = f + amp * rng.uniform(-1, 1) * np.cos(arg + phase)
         out[k] = f
     return out
+
+
+@dataclasses.dataclass(frozen=True)
+class AdjointRun:
+    """A differentiable 1-D run: initial fields blended from two (rho, u, P)
+    states, advanced nsteps steps, loss = dx * sum (n - target)^2."""
+    nx: int = 2048
+    Q: int = 8
+    gamma: float = 1.4
+    tau: float = 1e-5
+    dt: float = 2e-5
+    nsteps: int = 2000
+    every: int = 50
+    x0: float = -0.5
+    x1: float = 0.5
+    width: float = 0.05
+    states: tuple = (SOD_LEFT, SOD_RIGHT)
+    target_seed: int = 7
+
+    def params(self) -> np.ndarray:
+        """(rhoL, uL, PL, rhoR, uR, PR)."""
+        return np.asarray(self.states[0] + self.states[1], dtype=np.float64)
+
+    def spec(self) -> dict:
+        return {"nx": self.nx, "x0": self.x0, "x1": self.x1, "Q": self.Q, "dt": self.dt,
+                "nsteps": self.nsteps, "every": self.every}
+
+    def replace(self, **kw) -> "AdjointRun":
+        return dataclasses.replace(self, **kw)
+
+
+def adjoint_1d(**kw) -> AdjointRun:
+    return AdjointRun(**kw)
+
+
+def cell_centres(nx: int, x0: float, x1: float) -> np.ndarray:
+    return x0 + (np.arange(nx) + 0.5) * ((x1 - x0) / nx)
+
+
+def blend_states(params, x, width: float, tanh):
+    """rho, u, P = left + (right - left) s(x), s = (1 + tanh(x / width)) / 2.
+    params = (rhoL, uL, PL, rhoR, uR, PR); `tanh` is the array library's
+    (numpy.tanh or torch.tanh) so the same recipe serves both sides."""
+    s = 0.5 * (1.0 + tanh(x / width))
+    rho = params[0] + (params[3] - params[0]) * s
+    u = params[1] + (params[4] - params[1]) * s
+    P = params[2] + (params[5] - params[2]) * s
+    return rho, u, P
+
+
+def smooth_target(nx: int, x0: float = -0.5, x1: float = 0.5, seed: int = 7) -> np.ndarray:
+    """Seeded smooth density profile: a wide tanh step from about 1 to about
+    0.2 plus three low Fourier modes of amplitude up to 0.03."""
+    rng = np.random.default_rng(seed)
+    x = cell_centres(nx, x0, x1)
+    xc = rng.uniform(-0.1, 0.1)
+    f = 0.6 - 0.4 * np.tanh((x - xc) / 0.15)
+    for m in range(1, 4):
+        f = f + 0.03 * rng.uniform(-1, 1) * np.sin(2 * math.pi * m * (x - x0) + rng.uniform(0, 2 * math.pi))
+    return f
