@@ -85,6 +85,23 @@ typedef struct {
   double At[16], A[16], wt[4], w[4];
 } fdlb_tableau;
 
+/* Names for fdlb_named_tableau. */
+#define FDLB_TABLEAU_IMEX_SSP3_433 0   /* Table I (the tableau NULL selects) */
+#define FDLB_TABLEAU_EXPLICIT_SSPRK3 1 /* fully explicit comparator (Sec. VI) */
+
+/* Fill *out with a named tableau (host only; no GPU needed).
+ * FDLB_TABLEAU_EXPLICIT_SSPRK3 is the three-stage, third-order strong-
+ * stability-preserving Runge-Kutta method of Shu and Osher applied to the
+ * whole right-hand side, advection and collision alike (A = At, w = wt),
+ * written as a 4-stage tableau whose first two stages are F^n itself so that
+ * it runs through the same fused stage kernels.  With a_ii = 0 the closed-form
+ * relaxation reduces to the explicit one: F^(i) = R_i and
+ * dF^(i) = (dt/tau)(R_i - F_eq(R_i)).  Its real stability interval is about
+ * dt/tau <= 2.5, so it needs dt of the order of tau; the paper's conclusion
+ * (Sec. VI) quotes the IMEX step's dt/tau = 50 as the gain over such fully
+ * explicit schemes.  Returns FDLB_EINVAL for an unknown name or NULL out. */
+int fdlb_named_tableau(int which, fdlb_tableau* out);
+
 /* Create a context and allocate its device buffers on the current device.
  *   grid       : see fdlb_grid (nx, ny >= 1; x1 > x0; y1 > y0 when d = 2)
  *   Qphi, Qchi : Gauss-Hermite orders per axis; supported pairs (8,8), (5,3),

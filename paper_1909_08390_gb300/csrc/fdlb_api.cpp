@@ -147,6 +147,18 @@ void paper_tableau(fdlb_tableau* t) {
 
 // Reduce a supported tableau to the fused-stage coefficients (see
 // fdlb_internal.h for the algebra).
+// Shu-Osher SSP-RK3 on the whole right-hand side: stages F^n, F^n,
+// F^n + dt f(F^n), F^n + dt (f(F^n) + f(F^(3)))/4; weights (0, 1/6, 1/6, 2/3).
+void explicit_ssprk3_tableau(fdlb_tableau* t) {
+  std::memset(t, 0, sizeof *t);
+  t->r = 4;
+  t->At[2 * 4 + 1] = t->A[2 * 4 + 1] = 1.0;
+  t->At[3 * 4 + 1] = t->A[3 * 4 + 1] = 0.25;
+  t->At[3 * 4 + 2] = t->A[3 * 4 + 2] = 0.25;
+  t->wt[1] = t->wt[2] = t->w[1] = t->w[2] = 1.0 / 6.0;
+  t->wt[3] = t->w[3] = 2.0 / 3.0;
+}
+
 bool stage_coefficients(const fdlb_tableau& t, double lam, fdlb::StageCoef* sc, const char** why) {
   if (t.r != 4) { *why = "the fused kernels need r = 4 stages"; return false; }
   auto At = [&](int i, int j) { return t.At[i * 4 + j]; };
@@ -343,6 +355,14 @@ int ctx_launch_stage(fdlb_ctx* c, int stage, cudaStream_t s) { return launch_sta
 }  // namespace fdlb
 
 extern "C" {
+
+int fdlb_named_tableau(int which, fdlb_tableau* out) {
+  if (!out) return set_err(nullptr, FDLB_EINVAL, "out is NULL");
+  if (which == FDLB_TABLEAU_IMEX_SSP3_433) paper_tableau(out);
+  else if (which == FDLB_TABLEAU_EXPLICIT_SSPRK3) explicit_ssprk3_tableau(out);
+  else return set_err(nullptr, FDLB_EINVAL, "unknown tableau %d", which);
+  return FDLB_OK;
+}
 
 int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double tau, double dt,
                 const fdlb_tableau* tableau, int precision, void* cuda_stream, fdlb_ctx** out) {

@@ -33,6 +33,8 @@ FDLB_FP64 = 0
 FDLB_MIXED = 1
 FDLB_BC_OUTLET = 0
 FDLB_BC_PERIODIC = 1
+FDLB_TABLEAU_IMEX_SSP3_433 = 0
+FDLB_TABLEAU_EXPLICIT_SSPRK3 = 1
 
 _ERRNAMES = {0: "FDLB_OK", -1: "FDLB_EINVAL", -2: "FDLB_ECFL", -3: "FDLB_ENOMEM",
              -4: "FDLB_ECUDA", -5: "FDLB_EUNSTABLE", -6: "FDLB_ETIMEOUT"}
@@ -96,6 +98,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fdlb_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                   ctypes.POINTER(ctypes.c_int)]
     lib.fdlb_batch_set_tiling.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+    lib.fdlb_named_tableau.argtypes = [ctypes.c_int, ctypes.POINTER(fdlb_tableau)]
     lib.fdlb_init_fields.argtypes = [_vp, _vp, _vp, _vp]
     lib.fdlb_init_fields_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _dp]
     lib.fdlb_forward_ckpt.argtypes = [_vp, ctypes.c_int64, ctypes.c_int, _vp]
@@ -298,6 +301,20 @@ def fdlb_destroy(ctx):
 
 def fdlb_last_error(ctx=None) -> str:
     return load().fdlb_last_error(ctx).decode()
+
+
+def fdlb_named_tableau(which: int) -> fdlb_tableau:
+    t = fdlb_tableau()
+    _check(load().fdlb_named_tableau(int(which), ctypes.byref(t)), None)
+    return t
+
+
+def tableau_dict(t: fdlb_tableau) -> dict:
+    """The tableau as nested lists (At, A, wt, w), r x r."""
+    r = t.r
+    return {"At": [[t.At[i * r + j] for j in range(r)] for i in range(r)],
+            "A": [[t.A[i * r + j] for j in range(r)] for i in range(r)],
+            "wt": [t.wt[i] for i in range(r)], "w": [t.w[i] for i in range(r)]}
 
 
 def make_tableau(At, A, wt, w) -> fdlb_tableau:

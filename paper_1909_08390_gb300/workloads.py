@@ -14,6 +14,8 @@ Workloads (all inputs synthetic; the paper uses no dataset):
   rho in [0.1, 1.5], u, v in [-1.2, 1.2], P in [0.03, 1.5].
 * ``lax_liu_2d``: the paper's configurations 11 and 12 of the 2-D Riemann
   problem (Sec. V).
+* ``sod_paper``: the shock tube with the paper's Fig. 1 settings (Q = (5, 3),
+  tau = 1e-5, t = 0.15) and its resolution and time-step sweeps.
 * ``batched_1d``: independent two-state problems of uneven length and gamma.
 * ``adjoint_1d``: the shock-tube states joined by a smooth tanh blend of
   width 0.05 (so that the run is differentiable), Nx = 2048, Q = 8,
@@ -77,6 +79,22 @@ def sod_1d(nx: int = 400, Q: int = 8, Qchi: int | None = None, gamma: float = 1.
     """Shock tube: Nx = 400, Q = 8, gamma = 7/5, tau = 1e-6, dt = 5e-5, t = 0.1."""
     return Workload("sod_1d", 1, nx, 1, -0.5, 0.5, 0.0, 1.0, Q, Q if Qchi is None else Qchi,
                     gamma, tau, dt, t_end, (SOD_LEFT, SOD_RIGHT), 0.0, 0.0)
+
+
+# Sec. V's own shock-tube runs (Fig. 1): Q = (5, 3), K = 2 (gamma = 7/5),
+# tau = 1e-5, density profiles at t = 0.15.  (a): dt = 1e-5, S nodes swept;
+# (b): S = 400, dt swept.  dt = 5e-4 (dt/tau = 50) is the step the paper keeps.
+FIG1A_S = (200, 400, 800, 1600, 3200)
+FIG1A_DT = 1e-5
+FIG1B_S = 400
+FIG1B_DT = (1e-3, 5e-4, 1e-4, 5e-5, 1e-5)
+
+
+def sod_paper(S: int = 400, dt: float = 5e-4, tau: float = 1e-5, t_end: float = 0.15,
+              Qphi: int = 5, Qchi: int = 3) -> Workload:
+    """The shock tube as the paper runs it in Fig. 1 (8 populations)."""
+    return Workload("sod_paper", 1, S, 1, -0.5, 0.5, 0.0, 1.0, Qphi, Qchi, 1.4, tau, dt, t_end,
+                    (SOD_LEFT, SOD_RIGHT), 0.0, 0.0)
 
 
 # Seed of the 512 x 512 benchmark problem: the first seed whose four quadrant

@@ -90,3 +90,38 @@ def test_library_lattice_nodes(lib, Q):
     np.testing.assert_allclose(p, pn, rtol=0, atol=2e-13)
     np.testing.assert_allclose(w, wn / np.sqrt(2 * np.pi), rtol=1e-11)
     np.testing.assert_array_equal(p, -p[::-1])
+
+
+def test_named_tableaux(lib):
+    """fdlb_named_tableau: Table I as printed, and the explicit comparator
+    (Shu-Osher SSP-RK3 on the whole right-hand side) with its order
+    conditions and stability polynomial."""
+    import json
+    import os
+
+    import numpy as np
+
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "paper_values.json")))["tableau"]
+    imex = fdlb.tableau_dict(fdlb.fdlb_named_tableau(fdlb.FDLB_TABLEAU_IMEX_SSP3_433))
+    al, be, et = gold["alpha"], gold["beta"], gold["eta"]
+    assert imex["At"] == gold["At"] and imex["wt"] == gold["wt"] and imex["w"] == gold["w"]
+    A = np.array(imex["A"])
+    want = np.array([[al, 0, 0, 0], [-al, al, 0, 0], [0, 1 - al, al, 0],
+                     [be, et, 0.5 - be - et - al, al]])
+    assert np.array_equal(A, want)
+
+    ex = fdlb.tableau_dict(fdlb.fdlb_named_tableau(fdlb.FDLB_TABLEAU_EXPLICIT_SSPRK3))
+    assert ex["At"] == ex["A"] and ex["wt"] == ex["w"]
+    A, b = np.array(ex["A"]), np.array(ex["w"])
+    assert np.all(np.triu(A) == 0)  # explicit: strictly lower triangular
+    assert np.all(A[:, 0] == 0) and b[0] == 0 and np.all(A[1] == 0)  # the fused kernels' form
+    c = A.sum(1)
+    for got, exact in ((b.sum(), 1.0), (b @ c, 0.5), (b @ c ** 2, 1 / 3), (b @ A @ c, 1 / 6)):
+        assert abs(got - exact) < 1e-15
+    # stability function 1 + z b^T (I - zA)^-1 1 = 1 + z + z^2/2 + z^3/6 (order 3, 3 stages)
+    for z in (-0.5, -1.0, -2.5, 0.3):
+        R = 1 + z * b @ np.linalg.solve(np.eye(4) - z * A, np.ones(4))
+        assert abs(R - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-14
+    with pytest.raises(fdlb.FdlbError):
+        fdlb.fdlb_named_tableau(7)

@@ -183,6 +183,35 @@ def test_pure_relaxation_follows_implicit_stability_function(oracle, lam):
     np.testing.assert_allclose(F1, expect, rtol=0, atol=1e-14 * np.abs(F0).max() * max(1, lam))
 
 
+# Shu-Osher SSP-RK3 on the whole right-hand side as a 4-stage tableau (stages
+# F^n, F^n, F^n + dt f(F^n), F^n + dt (f(F^n) + f(F^(3)))/4): the fully
+# explicit comparator of Sec. VI's dt/tau claim
+SSPRK3 = {"At": [[0, 0, 0, 0], [0, 0, 0, 0], [0, 1, 0, 0], [0, 0.25, 0.25, 0]],
+          "A": [[0, 0, 0, 0], [0, 0, 0, 0], [0, 1, 0, 0], [0, 0.25, 0.25, 0]],
+          "wt": [0, 1 / 6, 1 / 6, 2 / 3], "w": [0, 1 / 6, 1 / 6, 2 / 3]}
+
+
+@pytest.mark.parametrize("lam", [0.5, 1.0, 2.0, 2.5, 3.0])
+def test_explicit_comparator_relaxation_is_taylor_polynomial(oracle, lam):
+    """With the explicit tableau, spatially uniform non-equilibrium data relax
+    by the cubic Taylor polynomial of exp(z), z = -dt/tau, per step: stable
+    (|R| <= 1) for dt/tau up to about 2.51 and growing beyond."""
+    pr = oracle.Problem(d=1, nx=8, bc=1, Qphi=8, Qchi=8, gamma=1.4, tau=1.0, dt=lam,
+                        tableau=SSPRK3)
+    rng = np.random.default_rng(4)
+    feq = oracle.equilibrium(pr, 1.1, [-0.2], 0.9)
+    pert = rng.uniform(-0.05, 0.05, size=pr.npop) * feq.max()
+    F0 = np.repeat((feq + pert)[:, None], pr.nx, axis=1)
+    n, u, _, T = oracle.moments(pr, F0)
+    feq0 = oracle.equilibrium(pr, n[0], [u[0]], T[0])
+    F1 = oracle.step(pr, F0, 1)
+    z = -lam
+    R = 1 + z + z * z / 2 + z ** 3 / 6
+    np.testing.assert_allclose(F1, feq0[:, None] + R * (F0 - feq0[:, None]), rtol=0,
+                               atol=1e-14 * np.abs(F0).max() * max(1, lam ** 3))
+    assert (abs(R) <= 1.0) == (lam <= 2.5)
+
+
 @pytest.mark.parametrize("p_sign", [1, -1])
 @pytest.mark.parametrize("theta_cells", [32, 64])
 def test_linear_advection_follows_explicit_stability_function(oracle, p_sign, theta_cells):
