@@ -475,7 +475,10 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
   const size_t esize = precision == FDLB_MIXED ? sizeof(float) : sizeof(double);
   const size_t arr = (size_t)p.P * (size_t)N * esize;
   const size_t mom_bytes = 4 * (size_t)N * sizeof(double);
-  c->buf_bytes = 6 * arr + mom_bytes + 256;
+  // binary32 contexts: three per-cell equilibrium records (fdlb_mixed.cu)
+  p.recw = precision == FDLB_MIXED ? fdlb::mixed_record_width(g.d, Qphi, Qchi) : 0;
+  const size_t rec_bytes = ((size_t)p.recw * (size_t)N * sizeof(float) + 255) / 256 * 256;
+  c->buf_bytes = 6 * arr + mom_bytes + 256 + 3 * rec_bytes;
   e = cudaMalloc(&c->buf, c->buf_bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -493,7 +496,10 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
   p.D = b + 5 * arr;
   c->mom = (double*)(b + 6 * arr);
   p.status = (unsigned*)(b + 6 * arr + mom_bytes);
+  for (int i = 0; i < 3; ++i)
+    p.erec[i] = p.recw ? (float*)(b + 6 * arr + mom_bytes + 256 + i * rec_bytes) : nullptr;
   e = cudaMallocHost(&c->status_host, sizeof(unsigned));
+  if (e == cudaSuccess && precision == FDLB_MIXED) e = (cudaError_t)fdlb::mixed_setup(p);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->buf, 0, c->buf_bytes, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
@@ -757,7 +763,9 @@ int fdlb_create_batch(int nprob, const int64_t* nx, const double* gamma, double 
   const size_t arr = (size_t)p.P * (size_t)total * esize;
   const size_t mom_bytes = 4 * (size_t)total * sizeof(double);
   const size_t pstat_bytes = ((size_t)nprob * sizeof(unsigned) + 255) / 256 * 256;
-  c->buf_bytes = 6 * arr + mom_bytes + 256 + pstat_bytes;
+  p.recw = precision == FDLB_MIXED ? fdlb::mixed_record_width(1, Qphi, Qchi) : 0;
+  const size_t rec_bytes = ((size_t)p.recw * (size_t)total * sizeof(float) + 255) / 256 * 256;
+  c->buf_bytes = 6 * arr + mom_bytes + 256 + pstat_bytes + 3 * rec_bytes;
   e = cudaMalloc(&c->buf, c->buf_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->probs_dev, nprob * sizeof(fdlb::BatchProblem));
   if (e != cudaSuccess) {
@@ -775,8 +783,12 @@ int fdlb_create_batch(int nprob, const int64_t* nx, const double* gamma, double 
   c->mom = (double*)(b + 6 * arr);
   p.status = (unsigned*)(b + 6 * arr + mom_bytes);
   p.pstatus = (unsigned*)(b + 6 * arr + mom_bytes + 256);
+  for (int i = 0; i < 3; ++i)
+    p.erec[i] = p.recw ? (float*)(b + 6 * arr + mom_bytes + 256 + pstat_bytes + i * rec_bytes)
+                       : nullptr;
   p.probs = c->probs_dev;
   e = cudaMallocHost(&c->status_host, sizeof(unsigned));
+  if (e == cudaSuccess && precision == FDLB_MIXED) e = (cudaError_t)fdlb::mixed_setup(p);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->buf, 0, c->buf_bytes, c->stream);
   if (e != cudaSuccess) {
     int r = cuda_err(nullptr, e, "batch set-up");

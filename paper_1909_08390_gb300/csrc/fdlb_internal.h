@@ -81,6 +81,10 @@ struct DevParams {
   int nprob, nwork;
   int variant;  // 1-D tile shape of the batch kernels (0, 1, 2)
   int bgrid;    // persistent grid size of the batch kernels
+  // FDLB_MIXED: per-cell records of the binary64 equilibrium factors, stored
+  // as binary32 (recw components x N each), of F^n, R3 and R4 (fdlb_mixed.cu)
+  float* erec[3];
+  int recw;
 };
 
 // 1-D tile shapes of the batch kernels, indexed by DevParams::variant:
@@ -101,5 +105,12 @@ int launch_moments(const DevParams& p, double* n, double* ux, double* uy, double
 // batch kernels (d = 1, several problems in one launch)
 int launch_batch_stage(const DevParams& p, int stage, cudaStream_t s);
 int launch_batch_init(const DevParams& p, cudaStream_t s);
+// binary32 single-pass stage kernels (fdlb_mixed.cu), single problems and
+// batches; mixed_setup raises the kernels' shared-memory limit (call once
+// before the first launch, outside stream capture)
+int mixed_record_width(int d, int Qp, int Qc);
+int mixed_setup(const DevParams& p);
+int launch_mixed_stage(const DevParams& p, int stage, cudaStream_t s);
+int launch_mixed_batch_stage(const DevParams& p, int stage, cudaStream_t s);
 
 }  // namespace fdlb

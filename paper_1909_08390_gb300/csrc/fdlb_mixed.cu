@@ -1,0 +1,493 @@
+// fdlb_mixed.cu -- binary32 stage kernels of the IMEX step (FDLB_MIXED):
+// one pass over memory per advected stage.
+//
+// The binary64 kernels (fdlb_kernels.cu) relax a stage in a second pass over
+// values parked in the output arrays, because the equilibrium of a cell needs
+// the moments of all its populations.  Here the relaxation of stage i is
+// applied by the kernel of stage i+1, when it loads the advected array:
+//   * every kernel writes the unrelaxed explicit part R_i of its stage, sums
+//     the moments of R_i per cell (Eq. Moments_discrete, compensated binary32
+//     pairs folded into binary64), and stores a record of the cell's
+//     equilibrium factors (Eq. gExpanded, binary64 arithmetic rounded once to
+//     binary32);
+//   * the next kernel forms the relaxed values from R_i and the record as it
+//     stages the tile and its halo (Sec. III closed forms):
+//       stage 3 stages F2 = E0 + c2 (F^n - E0) from F^n,
+//       stage 4 stages F3 = R3 - a33 e3 (R3 - E3) from R3,
+//       the final stage stages F4 = R4 - a44 e4 (R4 - E4) from R4,
+//     and uses D = F^n - E0, D3 = R3 - E3, D4 = R4 - E4 at its own cells.
+// Arrays read and written per population and step: stage 3 reads F^n and
+// writes R3, A4', Af'; stage 4 reads R3, A4', Af' and writes R4, Af''; the
+// final stage reads R4, Af'' and writes F^{n+1} -- 6 reads and 6 writes of
+// 4 bytes, plus one record per cell and kernel.
+#include "fdlb_device.cuh"
+
+namespace fdlb {
+namespace {
+
+// Components of a cell's record.  phi^eq(kx, ky) = A[kx] * B[ky] with
+// A = n g_x, B = g_y (1-D: A[k]); chi^eq(qx, qy) = C * A[qx] * B[qy] with
+// C = (D+K-d) T when Qchi = Qphi, else Hx[qx] * Hy[qy] with Hx = nchi h_x.
+template <int DIM, int QP, int QC>
+struct RecLayout {
+  static constexpr bool kSame = QP == QC;
+  static constexpr int kChi = DIM == 1 ? QP : 2 * QP;  // first chi component
+  static constexpr int W = kSame ? kChi + 1 : kChi + (DIM == 1 ? QC : 2 * QC);
+};
+
+// Equilibrium of population pop from a record whose components lie `stride`
+// floats apart (read through the read-only data cache).
+template <int DIM, int QP, int QC>
+__device__ __forceinline__ float eq_from_rec(const float* __restrict__ rec, int64_t stride,
+                                             int pop) {
+  using R = RecLayout<DIM, QP, QC>;
+  using L = Lat<DIM, QP, QC>;
+  if (pop < L::NPHI) {
+    if constexpr (DIM == 1) return rec[pop * stride];
+    else return rec[(pop % QP) * stride] * rec[(QP + pop / QP) * stride];
+  }
+  const int q = pop - L::NPHI;
+  if constexpr (R::kSame) {
+    if constexpr (DIM == 1) return rec[R::kChi * stride] * rec[q * stride];
+    else return rec[R::kChi * stride] * (rec[(q % QP) * stride] * rec[(QP + q / QP) * stride]);
+  } else {
+    if constexpr (DIM == 1) return rec[(R::kChi + q) * stride];
+    else return rec[(R::kChi + q % QC) * stride] * rec[(R::kChi + QC + q / QC) * stride];
+  }
+}
+
+// Record of the equilibrium of (n, u, T) at cell `cell` of rec (components N
+// apart).
+template <int DIM, int QP, int QC>
+__device__ __forceinline__ void write_record(const DevParams& p, double kchi, double n, double ux,
+                                             double uy, double T, float* __restrict__ rec,
+                                             int64_t cell, int64_t N) {
+  using R = RecLayout<DIM, QP, QC>;
+  double g[QP];
+  axis_g<QP>(p.wHp, ux, T, g);
+#pragma unroll
+  for (int k = 0; k < QP; ++k) rec[k * N + cell] = (float)(n * g[k]);
+  if constexpr (DIM == 2) {
+    axis_g<QP>(p.wHp, uy, T, g);
+#pragma unroll
+    for (int k = 0; k < QP; ++k) rec[(QP + k) * N + cell] = (float)g[k];
+  }
+  if constexpr (R::kSame) {
+    rec[R::kChi * N + cell] = (float)(kchi * T);
+  } else {
+    const double nchi = kchi * T * n;
+    double h[QC];
+    axis_g<QC>(p.wHc, ux, T, h);
+#pragma unroll
+    for (int q = 0; q < QC; ++q) rec[(R::kChi + q) * N + cell] = (float)(nchi * h[q]);
+    if constexpr (DIM == 2) {
+      axis_g<QC>(p.wHc, uy, T, h);
+#pragma unroll
+      for (int q = 0; q < QC; ++q) rec[(R::kChi + QC + q) * N + cell] = (float)h[q];
+    }
+  }
+}
+
+// Moments of a cell -> validity flags and record.
+template <int DIM, int QP, int QC>
+__device__ __forceinline__ void finish_cell(const DevParams& p, const Geo& geo,
+                                            const MomentsF& m, float* __restrict__ rec,
+                                            int64_t cell) {
+  double n, ux, uy, T;
+  if (!moments_to_nut<DIM>(geo.invDK, to_fp64(m), n, ux, uy, T)) {
+    atomicOr(p.status, 1u);
+    if (geo.prob >= 0) atomicOr(&p.pstatus[geo.prob], 1u);
+  }
+  write_record<DIM, QP, QC>(p, geo.kchi, n, ux, uy, T, rec, cell, p.N);
+}
+
+// Asynchronous 4-byte global -> shared copies (prefetch of the next group).
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int DIM, int QP, int QC, int VAR>
+struct MixSmem {
+  using C = TileCfg<DIM, VAR>;
+  static constexpr int SXH = C::TX + 2 * H;             // staged columns
+  static constexpr int SX = SXH + (DIM == 2 ? 1 : 0);   // tile row pitch
+  static constexpr int SY = DIM == 2 ? C::TY + 2 * H : 1;
+  static constexpr int NST = SY * SXH;                  // staged cells
+  float raw[C::G][NST];                // the group's advected values as loaded
+  float tile[C::G][SY][SX];            // relaxed advected populations
+  float hx[C::G][C::TY][C::TX + 1];    // interface values along x
+  float hy[DIM == 2 ? C::G : 1][DIM == 2 ? C::TX : 1][C::TY + 1];
+  float ownv[C::G][C::TY * C::TX];     // stage 3: F^n of the own cells
+  float ownd[C::G][C::TY * C::TX];     // R - F_eq of the own cells
+};
+
+// One tile of one stage.  Ends with every thread past its last use of the
+// shared memory, so a persistent CTA may start its next tile at once.
+template <int DIM, int QP, int QC, int STAGE, int VAR>
+__device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, int x0, int y0,
+                                           MixSmem<DIM, QP, QC, VAR>& sm) {
+  using C = TileCfg<DIM, VAR>;
+  using L = Lat<DIM, QP, QC>;
+  using M = MixSmem<DIM, QP, QC, VAR>;
+  constexpr int TX = C::TX, TY = C::TY, NT = C::NT, G = C::G, SEG = C::SEG;
+  constexpr int SX = M::SX, SXH = M::SXH, NST = M::NST;
+  constexpr int CELLS = TX * TY;
+  constexpr int CPT = (CELLS + NT - 1) / NT;
+  constexpr int NSEG = (TX + 1) / SEG;
+  static_assert(NSEG * SEG == TX + 1, "segments tile the line");
+  constexpr int NLINE = DIM == 2 ? TX + TY : 1;
+  static_assert(G * NLINE * NSEG == NT, "one march task per thread");
+  constexpr int J = (NST + NT - 1) / NT;  // staged cells per thread
+
+  float* __restrict__ const F = (float*)p.F;
+  float* __restrict__ const R3 = (float*)p.F3;
+  float* __restrict__ const A4 = (float*)p.A4;
+  float* __restrict__ const Af = (float*)p.Af;
+  const float* __restrict__ const rin =
+      p.erec[STAGE == kStage3 ? 0 : (STAGE == kStage4 ? 1 : 2)];
+  float* __restrict__ const rout = p.erec[STAGE == kStage3 ? 1 : (STAGE == kStage4 ? 2 : 0)];
+  const float* __restrict__ const adv = STAGE == kStage3 ? F : (STAGE == kStage4 ? R3 : A4);
+  const int tid = threadIdx.x;
+  const int64_t N = p.N;
+
+  // this thread's staged cells: tile offset, cell offset from geo.base
+  // (-1: none), own-cell index (-1: halo)
+  int soff[J], goff[J], oidx[J];
+#pragma unroll
+  for (int j = 0; j < J; ++j) {
+    const int e = tid + j * NT;
+    const int r = e / SXH, c = e % SXH;
+    soff[j] = r * SX + c;
+    goff[j] = -1;
+    oidx[j] = -1;
+    // 2-D: the corner blocks of the halo feed no line and are not loaded
+    const bool corner = DIM == 2 && (r < H || r >= H + TY) && (c < H || c >= H + TX);
+    if (e < NST && !corner) {
+      const int gx = wrap_or_clamp(x0 - H + c, geo.nx, p.bc);
+      const int gy = DIM == 2 ? wrap_or_clamp(y0 - H + r, geo.ny, p.bc) : 0;
+      goff[j] = gy * geo.nx + gx;
+      const int lx = c - H, ly = DIM == 2 ? r - H : 0;
+      if (lx >= 0 && lx < TX && ly >= 0 && ly < TY && x0 + lx < geo.nx && y0 + ly < geo.ny)
+        oidx[j] = ly * TX + lx;
+    }
+  }
+  // own cells of this thread (pass 1)
+  int lxs[CPT], lys[CPT];
+  int64_t cell[CPT];
+  bool valid[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int c = tid + k * NT;
+    lxs[k] = c % TX;
+    lys[k] = c / TX;
+    valid[k] = (c < CELLS) && (x0 + lxs[k] < geo.nx) && (y0 + lys[k] < geo.ny);
+    cell[k] = geo.base + (int64_t)(y0 + lys[k]) * geo.nx + (x0 + lxs[k]);
+  }
+  MomentsF mom[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) mom[k] = {};
+  const CoefS<float> sc(p.sc);
+  const float arelax = STAGE == kStage3 ? sc.c2 : (STAGE == kStage4 ? sc.a33e3 : sc.a44e4);
+  const float dtdx = (float)geo.dtdx, dtdy = (float)geo.dtdy;
+  const float* __restrict__ const rbase = rin + geo.base;
+
+  const int tg = tid / (NLINE * NSEG);
+  const int tline = (tid / NSEG) % NLINE;
+  const int tseg = tid % NSEG;
+  // each thread copies, and later reads, only its own staged cells, so its
+  // own wait on the copies orders them
+  auto prefetch = [&](int gfirst) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int pop = gfirst + g;
+      if (pop >= L::P) break;
+      const float* __restrict__ src = adv + (int64_t)pop * N + geo.base;
+#pragma unroll
+      for (int j = 0; j < J; ++j)
+        if (goff[j] >= 0) cp_async4(&sm.raw[g][tid + j * NT], src + goff[j]);
+    }
+    cp_async_commit();
+  };
+  prefetch(0);
+  for (int g0 = 0; g0 < L::P; g0 += G) {
+    // the running explicit parts of the own cells (stage 4, final), early
+    float a4v[CPT][G], afv[CPT][G];
+    if constexpr (STAGE != kStage3) {
+#pragma unroll
+      for (int k = 0; k < CPT; ++k)
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const int pop = g0 + g;
+          const bool ok = valid[k] && pop < L::P;
+          const int64_t e = (int64_t)pop * N + cell[k];
+          a4v[k][g] = (STAGE == kStage4 && ok) ? A4[e] : 0.0f;
+          afv[k][g] = ok ? Af[e] : 0.0f;
+        }
+    }
+    // ---- stage the group: relaxed advected values on tile + halo
+    cp_async_wait_all();
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int pop = g0 + g;
+      if (pop >= L::P) break;
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        if (goff[j] < 0) continue;
+        const float v = sm.raw[g][tid + j * NT];
+        const float fe = eq_from_rec<DIM, QP, QC>(rbase + goff[j], N, pop);
+        const float d = v - fe;
+        // stage 3: F2 = E0 + c2 D; stages 4, final: F = R - a_ii e_i (R - F_eq)
+        const float w = STAGE == kStage3 ? fmaf(arelax, d, fe) : fmaf(-arelax, d, v);
+        (&sm.tile[g][0][0])[soff[j]] = w;
+        if (oidx[j] >= 0) {
+          sm.ownd[g][oidx[j]] = d;
+          if (STAGE == kStage3) sm.ownv[g][oidx[j]] = v;
+        }
+      }
+    }
+    __syncthreads();
+    if (g0 + G < L::P) prefetch(g0 + G);  // overlaps the march and pass 1
+    // ---- every interface value once, marching upwind -> downwind
+    {
+      const int pop = g0 + tg;
+      const bool xline = (DIM == 1) || (tline < TY);
+      const float pv = (pop < L::P) ? (xline ? p.pxh[pop] : p.pyh[pop]) : 0.0f;
+      const int sgn = (pv >= 0.0f) ? 1 : -1;
+      const int i0 = tseg * SEG;
+      const int first = (sgn > 0) ? i0 : i0 + SEG - 1;
+      const int up = ((sgn > 0) ? first - 1 : first) + H;
+      const int r = (DIM == 2 && xline) ? tline : 0;
+      const int c = xline ? 0 : tline - TY;
+      const float* base = xline ? &sm.tile[tg][r + (DIM == 2 ? H : 0)][up] : &sm.tile[tg][up][c + H];
+      const int stride = xline ? 1 : SX;
+      float* out = xline ? &sm.hx[tg][r][first] : &sm.hy[tg][c][first];
+      mp9_march<SEG>(base, sgn * stride, out, sgn);
+    }
+    __syncthreads();
+    // ---- flux difference and explicit part of the own cells
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+      if (!valid[k]) continue;
+      const int lx = lxs[k], ly = lys[k], o = ly * TX + lx;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int pop = g0 + g;
+        if (pop >= L::P) break;
+        float X = (dtdx * p.pxh[pop]) * (sm.hx[g][ly][lx + 1] - sm.hx[g][ly][lx]);
+        if constexpr (DIM == 2)
+          X = fmaf(dtdy * p.pyh[pop], sm.hy[g][lx][ly + 1] - sm.hy[g][lx][ly], X);
+        const int64_t e = (int64_t)pop * N + cell[k];
+        const float d = sm.ownd[g][o];
+        float R;
+        if constexpr (STAGE == kStage3) {
+          const float f = sm.ownv[g][o];
+          R = fmaf(-sc.at32, X, fmaf(-sc.k3, d, f));
+          R3[e] = R;
+          A4[e] = fmaf(-sc.at42, X, fmaf(-sc.k4, d, f));
+          Af[e] = fmaf(-sc.wt2, X, fmaf(-sc.kf, d, f));
+        } else if constexpr (STAGE == kStage4) {
+          R = fmaf(-sc.at43, X, fmaf(-sc.a43e3, d, a4v[k][g]));
+          A4[e] = R;
+          Af[e] = fmaf(-sc.wt3, X, fmaf(-sc.w3e3, d, afv[k][g]));
+        } else {
+          R = fmaf(-sc.wt4, X, fmaf(-sc.w4e4, d, afv[k][g]));
+          F[e] = R;
+        }
+        accumulate<DIM, QP, QC>(p, mom[k], pop, R);
+      }
+    }
+    __syncthreads();
+  }
+  // ---- records of the stage's explicit parts (the next kernel relaxes them)
+#pragma unroll
+  for (int k = 0; k < CPT; ++k)
+    if (valid[k]) finish_cell<DIM, QP, QC>(p, geo, mom[k], rout, cell[k]);
+}
+
+template <int DIM, int QP, int QC, int STAGE>
+__global__ void __launch_bounds__(TileCfg<DIM>::NT, DIM == 2 ? 5 : 8)
+    mixed_stage_kernel(const __grid_constant__ DevParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  auto& sm = *reinterpret_cast<MixSmem<DIM, QP, QC, 0>*>(smraw);
+  const Geo geo{p.nx, p.ny, 0, p.kchi, p.invDK, p.dtdx, p.dtdy, -1};
+  mixed_tile<DIM, QP, QC, STAGE, 0>(p, geo, blockIdx.x * TileCfg<DIM>::TX,
+                                    blockIdx.y * TileCfg<DIM>::TY, sm);
+}
+
+template <int QP, int QC, int STAGE, int VAR>
+__global__ void __launch_bounds__(TileCfg<1, VAR>::NT, 4)
+    mixed_batch_kernel(const __grid_constant__ DevParams p) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  auto& sm = *reinterpret_cast<MixSmem<1, QP, QC, VAR>*>(smraw);
+  for (int w = blockIdx.x; w < p.nwork; w += gridDim.x) {
+    const WorkItem it = p.work[w];
+    const BatchProblem& bp = p.probs[it.prob];
+    const Geo geo{bp.nx, 1, bp.base, bp.kchi, bp.invDK, bp.dtdx, 0.0, it.prob};
+    mixed_tile<1, QP, QC, STAGE, VAR>(p, geo, it.x0, 0, sm);
+  }
+}
+
+// problem of cell c (problems sorted by base)
+__device__ __forceinline__ int problem_of(const DevParams& p, int64_t c) {
+  int lo = 0, hi = p.nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (p.probs[mid].base <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// The record of F^n (after fdlb_init_riemann or fdlb_set_state): the same
+// moment sums, in the same population order, as the final stage's.
+template <int DIM, int QP, int QC>
+__global__ void mixed_prep_kernel(const __grid_constant__ DevParams p) {
+  using L = Lat<DIM, QP, QC>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const float* F = (const float*)p.F;
+  MomentsF m = {};
+  for (int pop = 0; pop < L::P; ++pop) accumulate<DIM, QP, QC>(p, m, pop, F[pop * p.N + c]);
+  Geo geo{p.nx, p.ny, 0, p.kchi, p.invDK, p.dtdx, p.dtdy, -1};
+  if (p.nprob > 0) {
+    const int b = problem_of(p, c);
+    geo.kchi = p.probs[b].kchi;
+    geo.invDK = p.probs[b].invDK;
+    geo.prob = b;
+  }
+  finish_cell<DIM, QP, QC>(p, geo, m, p.erec[0], c);
+}
+
+template <int DIM, int QP, int QC>
+int setup_t() {
+  cudaError_t e = cudaSuccess;
+  const int b = (int)sizeof(MixSmem<DIM, QP, QC, 0>);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage3>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage4>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kFinal>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return (int)e;
+}
+
+template <int QP, int QC, int VAR>
+int setup_batch_v() {
+  cudaError_t e = cudaSuccess;
+  const int b = (int)sizeof(MixSmem<1, QP, QC, VAR>);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mixed_batch_kernel<QP, QC, kStage3, VAR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mixed_batch_kernel<QP, QC, kStage4, VAR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(mixed_batch_kernel<QP, QC, kFinal, VAR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return (int)e;
+}
+
+template <int DIM, int QP, int QC>
+int launch_t(const DevParams& p, int stage, cudaStream_t s) {
+  using C = TileCfg<DIM>;
+  if (stage == kPrep) {
+    const int nt = 128;
+    const int64_t nb = (p.N + nt - 1) / nt;
+    mixed_prep_kernel<DIM, QP, QC><<<(unsigned)nb, nt, 0, s>>>(p);
+    return (int)cudaGetLastError();
+  }
+  const dim3 grid((p.nx + C::TX - 1) / C::TX, DIM == 2 ? (p.ny + C::TY - 1) / C::TY : 1);
+  const size_t b = sizeof(MixSmem<DIM, QP, QC, 0>);
+  switch (stage) {
+    case kStage3: mixed_stage_kernel<DIM, QP, QC, kStage3><<<grid, C::NT, b, s>>>(p); break;
+    case kStage4: mixed_stage_kernel<DIM, QP, QC, kStage4><<<grid, C::NT, b, s>>>(p); break;
+    default: mixed_stage_kernel<DIM, QP, QC, kFinal><<<grid, C::NT, b, s>>>(p); break;
+  }
+  return (int)cudaGetLastError();
+}
+
+template <int QP, int QC, int VAR>
+int launch_batch_v(const DevParams& p, int stage, cudaStream_t s) {
+  using C = TileCfg<1, VAR>;
+  const int grid = p.bgrid > 0 ? p.bgrid : 1;
+  const size_t b = sizeof(MixSmem<1, QP, QC, VAR>);
+  switch (stage) {
+    case kStage3: mixed_batch_kernel<QP, QC, kStage3, VAR><<<grid, C::NT, b, s>>>(p); break;
+    case kStage4: mixed_batch_kernel<QP, QC, kStage4, VAR><<<grid, C::NT, b, s>>>(p); break;
+    default: mixed_batch_kernel<QP, QC, kFinal, VAR><<<grid, C::NT, b, s>>>(p); break;
+  }
+  return (int)cudaGetLastError();
+}
+
+template <int QP, int QC>
+int launch_batch_t(const DevParams& p, int stage, cudaStream_t s) {
+  if (stage == kPrep) {
+    const int nt = 128;
+    const int64_t nb = (p.N + nt - 1) / nt;
+    mixed_prep_kernel<1, QP, QC><<<(unsigned)nb, nt, 0, s>>>(p);
+    return (int)cudaGetLastError();
+  }
+  switch (p.variant) {
+    case 1: return launch_batch_v<QP, QC, 1>(p, stage, s);
+    case 2: return launch_batch_v<QP, QC, 2>(p, stage, s);
+    default: return launch_batch_v<QP, QC, 0>(p, stage, s);
+  }
+}
+
+}  // namespace
+
+int mixed_record_width(int d, int Qp, int Qc) {
+#define X(D_, P_, C_) \
+  if (d == D_ && Qp == P_ && Qc == C_) return RecLayout<D_, P_, C_>::W;
+  FDLB_LATTICES(X)
+#undef X
+  return 0;
+}
+
+int mixed_setup(const DevParams& p) {
+  if (p.nprob > 0) {
+#define X(P_, C_)                                                                   \
+  if (p.Qp == P_ && p.Qc == C_) {                                                   \
+    int e = setup_batch_v<P_, C_, 0>();                                             \
+    if (!e) e = setup_batch_v<P_, C_, 1>();                                         \
+    if (!e) e = setup_batch_v<P_, C_, 2>();                                         \
+    return e;                                                                       \
+  }
+    FDLB_BATCH_LATTICES(X)
+#undef X
+    return (int)cudaErrorInvalidValue;
+  }
+#define X(D_, P_, C_) \
+  if (p.d == D_ && p.Qp == P_ && p.Qc == C_) return setup_t<D_, P_, C_>();
+  FDLB_LATTICES(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_mixed_stage(const DevParams& p, int stage, cudaStream_t s) {
+#define X(D_, P_, C_) \
+  if (p.d == D_ && p.Qp == P_ && p.Qc == C_) return launch_t<D_, P_, C_>(p, stage, s);
+  FDLB_LATTICES(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_mixed_batch_stage(const DevParams& p, int stage, cudaStream_t s) {
+#define X(P_, C_) \
+  if (p.Qp == P_ && p.Qc == C_) return launch_batch_t<P_, C_>(p, stage, s);
+  FDLB_BATCH_LATTICES(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace fdlb
