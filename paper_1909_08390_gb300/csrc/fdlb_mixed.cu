@@ -113,6 +113,35 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Record prefetch plan of a population group, for lattices with Qchi = Qphi
+// whose groups align with rows of the velocity grid ((8, 8) with groups of 4
+// in 2-D; groups of 8 or 16 in 1-D).  Slot s of the group's buffer holds one
+// record component: slots 0..NA-1 the x factors A of the group's columns,
+// then (2-D) the y factor B of its row, then the chi factor C.
+template <int DIM, int QP, int QC, int G>
+struct GroupRec {
+  static constexpr bool kOn =
+      QP == QC && (DIM == 2 ? (QP % G == 0) : (QP % G == 0 || G % QP == 0));
+  static constexpr int NA = G < QP ? G : QP;
+  static constexpr int kB = NA;
+  static constexpr int kC = NA + (DIM == 2 ? 1 : 0);
+  static constexpr int NS = kC + 1;
+  // first x-factor component of group g0 (1-D groups of 2 QP start at 0)
+  __device__ static int a0(int g0) {
+    const int nphi = DIM == 2 ? QP * QP : QP;
+    const int k0 = g0 >= nphi ? g0 - nphi : g0;
+    return G > QP ? 0 : k0 % QP;
+  }
+  __device__ static bool has_chi(int g0) { return g0 + G > (DIM == 2 ? QP * QP : QP); }
+  // record component held by slot s for group g0 (-1: unused)
+  __device__ static int comp(int g0, int s) {
+    const int nphi = DIM == 2 ? QP * QP : QP;
+    if (s < NA) return a0(g0) + s;
+    if (DIM == 2 && s == kB) return QP + (g0 >= nphi ? g0 - nphi : g0) / QP;
+    return has_chi(g0) ? RecLayout<DIM, QP, QC>::kChi : -1;
+  }
+};
+
 template <int DIM, int QP, int QC, int VAR>
 struct MixSmem {
   using C = TileCfg<DIM, VAR>;
@@ -121,6 +150,9 @@ struct MixSmem {
   static constexpr int SY = DIM == 2 ? C::TY + 2 * H : 1;
   static constexpr int NST = SY * SXH;                  // staged cells
   float raw[C::G][NST];                // the group's advected values as loaded
+  // the group's record components (GroupRec plan), as loaded
+  float rbuf[GroupRec<DIM, QP, QC, C::G>::kOn ? GroupRec<DIM, QP, QC, C::G>::NS : 1]
+            [GroupRec<DIM, QP, QC, C::G>::kOn ? NST : 1];
   float tile[C::G][SY][SX];            // relaxed advected populations
   float hx[C::G][C::TY][C::TX + 1];    // interface values along x
   float hy[DIM == 2 ? C::G : 1][DIM == 2 ? C::TX : 1][C::TY + 1];
@@ -203,6 +235,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   const int tseg = tid % NSEG;
   // each thread copies, and later reads, only its own staged cells, so its
   // own wait on the copies orders them
+  using GR = GroupRec<DIM, QP, QC, G>;
   auto prefetch = [&](int gfirst) {
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -212,6 +245,17 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
 #pragma unroll
       for (int j = 0; j < J; ++j)
         if (goff[j] >= 0) cp_async4(&sm.raw[g][tid + j * NT], src + goff[j]);
+    }
+    if constexpr (GR::kOn) {
+#pragma unroll
+      for (int sl = 0; sl < GR::NS; ++sl) {
+        const int comp = GR::comp(gfirst, sl);
+        if (comp < 0) continue;
+        const float* __restrict__ src = rbase + (int64_t)comp * N;
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+          if (goff[j] >= 0) cp_async4(&sm.rbuf[sl][tid + j * NT], src + goff[j]);
+      }
     }
     cp_async_commit();
   };
@@ -240,8 +284,19 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
 #pragma unroll
       for (int j = 0; j < J; ++j) {
         if (goff[j] < 0) continue;
-        const float v = sm.raw[g][tid + j * NT];
-        const float fe = eq_from_rec<DIM, QP, QC>(rbase + goff[j], N, pop);
+        const int e = tid + j * NT;
+        const float v = sm.raw[g][e];
+        float fe;
+        if constexpr (GR::kOn) {
+          // same products, in the same order, as eq_from_rec
+          const int nphi = DIM == 2 ? QP * QP : QP;
+          const int k = pop >= nphi ? pop - nphi : pop;
+          const float a = sm.rbuf[(DIM == 2 ? k % QP : k) - GR::a0(g0)][e];
+          const float ab = DIM == 2 ? a * sm.rbuf[GR::kB][e] : a;
+          fe = pop >= nphi ? sm.rbuf[GR::kC][e] * ab : ab;
+        } else {
+          fe = eq_from_rec<DIM, QP, QC>(rbase + goff[j], N, pop);
+        }
         const float d = v - fe;
         // stage 3: F2 = E0 + c2 D; stages 4, final: F = R - a_ii e_i (R - F_eq)
         const float w = STAGE == kStage3 ? fmaf(arelax, d, fe) : fmaf(-arelax, d, v);
@@ -312,7 +367,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
 }
 
 template <int DIM, int QP, int QC, int STAGE>
-__global__ void __launch_bounds__(TileCfg<DIM>::NT, DIM == 2 ? 5 : 8)
+__global__ void __launch_bounds__(TileCfg<DIM>::NT, DIM == 2 ? 4 : 8)
     mixed_stage_kernel(const __grid_constant__ DevParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   auto& sm = *reinterpret_cast<MixSmem<DIM, QP, QC, 0>*>(smraw);
