@@ -46,8 +46,14 @@ FLOPS_PER_POP = {"stage3": 48 + 5 + 24, "stage4": 48 + 5 + 14, "final": 48 + 5 +
 # written once each by the kernel (stage 3: F2, F, D -> F3, A4, Af; stage 4:
 # F3, A4, Af -> A4, Af; final: A4, Af -> F, D, F2).
 BYTES_PER_POP = {"stage3": 6 * 8, "stage4": 5 * 8, "final": 5 * 8}
-# Mixed precision: the same arrays in binary32 (4 B per population).
-BYTES_PER_POP_MIXED = {k: v // 2 for k, v in BYTES_PER_POP.items()}
+# Mixed precision (single-pass kernels, 4 B per population): stage 3 reads
+# F^n and writes R3, A4', Af'; stage 4 reads R3, A4', Af' and writes R4, Af'';
+# the final stage reads R4, Af'' and writes F^{n+1}; plus, per cell, one
+# equilibrium record read and one written (17 binary32 values for the 8x8
+# lattice: 2 * 17 * 4 / 128 B per population).
+MIXED_RECORD_BYTES_PER_POP = 2 * 17 * 4 / 128
+BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
+                       for k, n in (("stage3", 4), ("stage4", 5), ("final", 3))}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # the ncu captures summarised in profiles/stage_kernel_fp64_quadrant512.md and
 # profiles/stage_kernel_mixed_quadrant512.md, valid for the kernel sources
@@ -415,7 +421,7 @@ def run_ours(args, world, rank, local):
             "err_vs_fp64": {"n": relerr(mn, fn), "u": relerr(mu, fu, 1.0),
                             "v": relerr(mv, fv, 1.0), "T": relerr(mT, fT),
                             "after_steps": args.warmup + args.steps},
-            "roofline": {"bound": "hbm", "kernel": f"stage_kernel<2,8,8,{names[mt]},float>",
+            "roofline": {"bound": "hbm", "kernel": f"mixed_stage_kernel<2,8,8,{names[mt]}>",
                          "achieved": m_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                          "frac": (m_gbs / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",

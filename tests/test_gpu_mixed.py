@@ -102,3 +102,37 @@ def test_mixed_conservation_periodic(F):
                                          (n * (ux * ux + uy * uy) + 5.0 * n * T).sum()])
     a, b = tot(n0, ux0, uy0, T0), tot(n1, ux1, uy1, T1)
     assert np.all(np.abs(a - b) <= 1e-5 * np.maximum(np.abs(a), 1.0)), (a, b)
+
+
+def test_mixed_2048_against_fp64_gpu(F):
+    """2048 x 2048 cells x 128 populations (2.1 GB per binary32 array) with the
+    benchmark seed's quadrant states, dt = 2.5e-5, tau = 1e-6: the mixed and
+    binary64 GPU runs agree to 1e-5 in n, u, v, T after 200 steps."""
+    wl = W.quadrant_2d(W.BENCH_SEED, n=2048)
+    out = {}
+    for prec in (F.FDLB_FP64, F.FDLB_MIXED):
+        with F.Solver.from_workload(wl, precision=prec) as s:
+            s.init_riemann(wl.states, 0.5, 0.5)
+            s.step(200)
+            out[prec] = s.moments()
+    err = fields_err(out[F.FDLB_MIXED], out[F.FDLB_FP64])
+    print("2048^2, 200 steps, mixed vs binary64:", err)
+    assert max(err.values()) < TOL, err
+
+
+def test_benchmark_seed_on_256_grid_against_oracle(F, oracle):
+    """The same seeded problem on 256 x 256 cells (the oracle's copy of the
+    2048^2 run): binary64 GPU within 1e-12 of the oracle, mixed within 1e-5,
+    after 8 steps."""
+    wl = W.quadrant_2d(W.BENCH_SEED, n=256)
+    pr = oracle.Problem(d=2, nx=256, ny=256, x0=0.0, x1=1.0, y0=0.0, y1=1.0, Qphi=8, Qchi=8,
+                        gamma=wl.gamma, tau=wl.tau, dt=wl.dt)
+    want = oracle.step(pr, oracle.init_states(pr, wl.states, 0.5, 0.5), 8)
+    om = oracle.moments(pr, want)
+    for prec, tol in ((F.FDLB_FP64, 1e-12), (F.FDLB_MIXED, TOL)):
+        with F.Solver.from_workload(wl, precision=prec) as s:
+            s.init_riemann(wl.states, 0.5, 0.5)
+            s.step(8)
+            err = fields_err(s.moments(), om)
+        print("256^2 vs oracle, precision", prec, err)
+        assert max(err.values()) < tol, (prec, err)
