@@ -314,6 +314,10 @@ int params_for(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double t
     return set_err(nullptr, FDLB_EINVAL, "Gauss-Hermite rule failed to converge");
   weighted_hermite_table(Qphi, p.pp, wp, p.wHp);
   weighted_hermite_table(Qchi, p.pc, wc, p.wHc);
+  for (int i = 0; i < kMaxQ * kMaxQ; ++i) {
+    split_float(p.wHp[i], &p.wHph[i], &p.wHpl[i]);
+    split_float(p.wHc[i], &p.wHch[i], &p.wHcl[i]);
+  }
   const double pmax = std::fmax(std::fabs(p.pp[Qphi - 1]), std::fabs(p.pc[Qchi - 1]));
   const double cfl = pmax * std::fmax(p.dtdx, p.dtdy);
   if (cfl > 1.0) return set_err(nullptr, FDLB_ECFL, "CFL = %g > 1", cfl);
@@ -433,6 +437,10 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
   }
   weighted_hermite_table(Qphi, p.pp, wp, p.wHp);
   weighted_hermite_table(Qchi, p.pc, wc, p.wHc);
+  for (int i = 0; i < kMaxQ * kMaxQ; ++i) {
+    split_float(p.wHp[i], &p.wHph[i], &p.wHpl[i]);
+    split_float(p.wHc[i], &p.wHch[i], &p.wHcl[i]);
+  }
   // CFL condition |p| dt / ds <= 1 for all momenta (Sec. IV)
   const double pmax = std::fmax(std::fabs(p.pp[Qphi - 1]), std::fabs(p.pc[Qchi - 1]));
   const double cfl = pmax * std::fmax(p.dtdx, p.dtdy);

@@ -59,6 +59,8 @@ struct DevParams {
   double pp[kMaxQ], pc[kMaxQ];  // phi and chi momenta (ascending)
   double wHp[kMaxQ * kMaxQ];    // [l*kMaxQ + k] = w_k He_l(p_k)/l!, phi axis
   double wHc[kMaxQ * kMaxQ];    // same for the chi axis
+  // the same tables as binary32 pairs hi + lo (the mixed path's records)
+  float wHph[kMaxQ * kMaxQ], wHpl[kMaxQ * kMaxQ], wHch[kMaxQ * kMaxQ], wHcl[kMaxQ * kMaxQ];
   double invDK;                 // 1 / (D + K)
   StageCoef sc;
   // per population: dt p_x/dx, dt p_y/dy, p_x, p_y, and p^2 (phi) or 0 (chi)

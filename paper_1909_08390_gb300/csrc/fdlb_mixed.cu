@@ -56,34 +56,100 @@ __device__ __forceinline__ float eq_from_rec(const float* __restrict__ rec, int6
   }
 }
 
+// ---- binary32 pairs: x = hi + lo with about 48 significant bits ----------
+// The records' Hermite factors are evaluated in this arithmetic on the
+// binary32 pipe.  GB300's binary64 pipe runs at 1/64 of the binary32 rate;
+// evaluated in binary64, the factors of a 1-D cell (16 populations) would
+// cost more pipe time than all of the cell's population work.  The pair
+// arithmetic is the classical error-free one (Dekker, Knuth): TwoSum for
+// additions, the fused multiply-add for the exact product error; the
+// intrinsics keep the compiler from contracting the error terms away.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_quick(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  const float s = __fadd_rn(x.hi, y.hi);
+  const float bb = __fsub_rn(s, x.hi);
+  const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+  return df_quick(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ DF df_neg(DF x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float pr = __fmul_rn(x.hi, y.hi);
+  float e = fmaf(x.hi, y.hi, -pr);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return df_quick(pr, e);
+}
+__device__ __forceinline__ DF df_of(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ float df_round(DF x) { return __fadd_rn(x.hi, x.lo); }
+
+// One axis of the equilibrium factors (Eq. gExpanded) times `scale`, in pair
+// arithmetic: the recurrence a_0 = s, a_1 = s u, a_l = u a_{l-1} +
+// (l-1)(T-1) a_{l-2}, then g_k = sum_l [w_k He_l(p_k)/l!] a_l, summed as even
+// and odd parts over the antisymmetric nodes like axis_g.
+template <int Q>
+__device__ __forceinline__ void axis_g_df(const float* ch, const float* cl, DF u, DF T, DF scale,
+                                          DF (&g)[Q]) {
+  DF a[Q];
+  a[0] = scale;
+  if (Q > 1) a[1] = df_mul(scale, u);
+  const DF tm1 = df_add(T, DF{-1.0f, 0.0f});
+#pragma unroll
+  for (int l = 2; l < Q; ++l)
+    a[l] = df_add(df_mul(u, a[l - 1]), df_mul(df_mul(DF{(float)(l - 1), 0.0f}, tm1), a[l - 2]));
+#pragma unroll
+  for (int k = 0; k < (Q + 1) / 2; ++k) {
+    DF e = df_mul(DF{ch[k], cl[k]}, a[0]);
+    DF o = DF{0.0f, 0.0f};
+#pragma unroll
+    for (int l = 1; l < Q; ++l) {
+      const DF t = df_mul(DF{ch[l * kMaxQ + k], cl[l * kMaxQ + k]}, a[l]);
+      if (l & 1) o = df_add(o, t);
+      else e = df_add(e, t);
+    }
+    g[k] = df_add(e, o);
+    if (Q - 1 - k != k) g[Q - 1 - k] = df_add(e, df_neg(o));
+  }
+}
+
 // Record of the equilibrium of (n, u, T) at cell `cell` of rec (components N
-// apart).
+// apart): n, u, T arrive in binary64 and the factors are formed in pair
+// arithmetic, then rounded once to binary32.
 template <int DIM, int QP, int QC>
 __device__ __forceinline__ void write_record(const DevParams& p, double kchi, double n, double ux,
                                              double uy, double T, float* __restrict__ rec,
                                              int64_t cell, int64_t N) {
   using R = RecLayout<DIM, QP, QC>;
-  double g[QP];
-  axis_g<QP>(p.wHp, ux, T, g);
+  const DF du = df_of(ux), dT = df_of(T), one{1.0f, 0.0f};
+  DF g[QP];
+  axis_g_df<QP>(p.wHph, p.wHpl, du, dT, df_of(n), g);
 #pragma unroll
-  for (int k = 0; k < QP; ++k) rec[k * N + cell] = (float)(n * g[k]);
+  for (int k = 0; k < QP; ++k) rec[k * N + cell] = df_round(g[k]);
   if constexpr (DIM == 2) {
-    axis_g<QP>(p.wHp, uy, T, g);
+    axis_g_df<QP>(p.wHph, p.wHpl, df_of(uy), dT, one, g);
 #pragma unroll
-    for (int k = 0; k < QP; ++k) rec[(QP + k) * N + cell] = (float)g[k];
+    for (int k = 0; k < QP; ++k) rec[(QP + k) * N + cell] = df_round(g[k]);
   }
   if constexpr (R::kSame) {
     rec[R::kChi * N + cell] = (float)(kchi * T);
   } else {
-    const double nchi = kchi * T * n;
-    double h[QC];
-    axis_g<QC>(p.wHc, ux, T, h);
+    DF h[QC];
+    axis_g_df<QC>(p.wHch, p.wHcl, du, dT, df_of(kchi * T * n), h);
 #pragma unroll
-    for (int q = 0; q < QC; ++q) rec[(R::kChi + q) * N + cell] = (float)(nchi * h[q]);
+    for (int q = 0; q < QC; ++q) rec[(R::kChi + q) * N + cell] = df_round(h[q]);
     if constexpr (DIM == 2) {
-      axis_g<QC>(p.wHc, uy, T, h);
+      axis_g_df<QC>(p.wHch, p.wHcl, df_of(uy), dT, one, h);
 #pragma unroll
-      for (int q = 0; q < QC; ++q) rec[(R::kChi + QC + q) * N + cell] = (float)h[q];
+      for (int q = 0; q < QC; ++q) rec[(R::kChi + QC + q) * N + cell] = df_round(h[q]);
     }
   }
 }
@@ -126,6 +192,7 @@ struct GroupRec {
   static constexpr int kB = NA;
   static constexpr int kC = NA + (DIM == 2 ? 1 : 0);
   static constexpr int NS = kC + 1;
+  static_assert(kB <= kC, "slot order");
   // first x-factor component of group g0 (1-D groups of 2 QP start at 0)
   __device__ static int a0(int g0) {
     const int nphi = DIM == 2 ? QP * QP : QP;
