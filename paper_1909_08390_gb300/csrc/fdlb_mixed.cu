@@ -122,49 +122,65 @@ __device__ __forceinline__ void axis_g_df(const float* ch, const float* cl, DF u
 }
 
 // Record of the equilibrium of (n, u, T) at cell `cell` of rec (components N
-// apart): n, u, T arrive in binary64 and the factors are formed in pair
-// arithmetic, then rounded once to binary32.
+// apart), in pair arithmetic, each component rounded once to binary32.
 template <int DIM, int QP, int QC>
-__device__ __forceinline__ void write_record(const DevParams& p, double kchi, double n, double ux,
-                                             double uy, double T, float* __restrict__ rec,
-                                             int64_t cell, int64_t N) {
+__device__ __forceinline__ void write_record(const DevParams& p, DF kchi, DF n, DF ux, DF uy, DF T,
+                                             float* __restrict__ rec, int64_t cell, int64_t N) {
   using R = RecLayout<DIM, QP, QC>;
-  const DF du = df_of(ux), dT = df_of(T), one{1.0f, 0.0f};
+  const DF one{1.0f, 0.0f};
   DF g[QP];
-  axis_g_df<QP>(p.wHph, p.wHpl, du, dT, df_of(n), g);
+  axis_g_df<QP>(p.wHph, p.wHpl, ux, T, n, g);
 #pragma unroll
   for (int k = 0; k < QP; ++k) rec[k * N + cell] = df_round(g[k]);
   if constexpr (DIM == 2) {
-    axis_g_df<QP>(p.wHph, p.wHpl, df_of(uy), dT, one, g);
+    axis_g_df<QP>(p.wHph, p.wHpl, uy, T, one, g);
 #pragma unroll
     for (int k = 0; k < QP; ++k) rec[(QP + k) * N + cell] = df_round(g[k]);
   }
+  const DF kT = df_mul(kchi, T);
   if constexpr (R::kSame) {
-    rec[R::kChi * N + cell] = (float)(kchi * T);
+    rec[R::kChi * N + cell] = df_round(kT);
   } else {
     DF h[QC];
-    axis_g_df<QC>(p.wHch, p.wHcl, du, dT, df_of(kchi * T * n), h);
+    axis_g_df<QC>(p.wHch, p.wHcl, ux, T, df_mul(kT, n), h);
 #pragma unroll
     for (int q = 0; q < QC; ++q) rec[(R::kChi + q) * N + cell] = df_round(h[q]);
     if constexpr (DIM == 2) {
-      axis_g_df<QC>(p.wHch, p.wHcl, df_of(uy), dT, one, h);
+      axis_g_df<QC>(p.wHch, p.wHcl, uy, T, one, h);
 #pragma unroll
       for (int q = 0; q < QC; ++q) rec[(R::kChi + QC + q) * N + cell] = df_round(h[q]);
     }
   }
 }
 
-// Moments of a cell -> validity flags and record.
+// Moments of a cell -> validity flags and record: n, u = j/n and
+// T = (E - j u)/((D+K) n) (Eq. Moments_discrete and the temperature
+// definition) from the compensated sums, in pair arithmetic.  The reciprocal
+// is one Newton step from the binary32 one.
 template <int DIM, int QP, int QC>
-__device__ __forceinline__ void finish_cell(const DevParams& p, const Geo& geo,
+__device__ __forceinline__ void finish_cell(const DevParams& p, DF kchi, DF invDK, int prob,
                                             const MomentsF& m, float* __restrict__ rec,
                                             int64_t cell) {
-  double n, ux, uy, T;
-  if (!moments_to_nut<DIM>(geo.invDK, to_fp64(m), n, ux, uy, T)) {
+  const DF zero{0.0f, 0.0f};
+  const DF n = df_add(DF{m.nh, 0.0f}, DF{m.nl, 0.0f});
+  const DF jx = df_add(DF{m.jxh, 0.0f}, DF{m.jxl, 0.0f});
+  const DF jy = DIM == 2 ? df_add(DF{m.jyh, 0.0f}, DF{m.jyl, 0.0f}) : zero;
+  const DF e = df_add(DF{m.eh, 0.0f}, DF{m.el, 0.0f});
+  const float r0 = __frcp_rn(n.hi);
+  const DF inv_n = df_add(DF{r0, 0.0f},
+                          df_mul(DF{r0, 0.0f}, df_add(DF{1.0f, 0.0f}, df_neg(df_mul(n, DF{r0, 0.0f})))));
+  const DF ux = df_mul(jx, inv_n);
+  const DF uy = DIM == 2 ? df_mul(jy, inv_n) : zero;
+  DF ke = df_add(e, df_neg(df_mul(jx, ux)));
+  if constexpr (DIM == 2) ke = df_add(ke, df_neg(df_mul(jy, uy)));
+  const DF T = df_mul(df_mul(ke, inv_n), invDK);
+  const bool ok = n.hi > 0.0f && T.hi > 0.0f && isfinite(n.hi) && isfinite(T.hi) &&
+                  isfinite(ux.hi) && isfinite(uy.hi);
+  if (!ok) {
     atomicOr(p.status, 1u);
-    if (geo.prob >= 0) atomicOr(&p.pstatus[geo.prob], 1u);
+    if (prob >= 0) atomicOr(&p.pstatus[prob], 1u);
   }
-  write_record<DIM, QP, QC>(p, geo.kchi, n, ux, uy, T, rec, cell, p.N);
+  write_record<DIM, QP, QC>(p, kchi, n, ux, uy, T, rec, cell, p.N);
 }
 
 // Asynchronous 4-byte global -> shared copies (prefetch of the next group).
@@ -295,6 +311,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   const CoefS<float> sc(p.sc);
   const float arelax = STAGE == kStage3 ? sc.c2 : (STAGE == kStage4 ? sc.a33e3 : sc.a44e4);
   const float dtdx = (float)geo.dtdx, dtdy = (float)geo.dtdy;
+  const DF kchi_df = df_of(geo.kchi), invDK_df = df_of(geo.invDK);
   const float* __restrict__ const rbase = rin + geo.base;
 
   const int tg = tid / (NLINE * NSEG);
@@ -430,7 +447,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   // ---- records of the stage's explicit parts (the next kernel relaxes them)
 #pragma unroll
   for (int k = 0; k < CPT; ++k)
-    if (valid[k]) finish_cell<DIM, QP, QC>(p, geo, mom[k], rout, cell[k]);
+    if (valid[k]) finish_cell<DIM, QP, QC>(p, kchi_df, invDK_df, geo.prob, mom[k], rout, cell[k]);
 }
 
 template <int DIM, int QP, int QC, int STAGE>
@@ -484,7 +501,7 @@ __global__ void mixed_prep_kernel(const __grid_constant__ DevParams p) {
     geo.invDK = p.probs[b].invDK;
     geo.prob = b;
   }
-  finish_cell<DIM, QP, QC>(p, geo, m, p.erec[0], c);
+  finish_cell<DIM, QP, QC>(p, df_of(geo.kchi), df_of(geo.invDK), geo.prob, m, p.erec[0], c);
 }
 
 template <int DIM, int QP, int QC>

@@ -47,8 +47,8 @@ def test_mixed_sod_1d_against_oracle(oracle, F):
     t = 0.1 gets 2e-5: its largest difference sits in the shock cell, where
     the binary32 rounding of every stored population (6e-8 relative, four
     stages per step) accumulates to about 1e-5 whatever the record arithmetic
-    (measured 9.5e-6 with binary64 record factors, 1.0e-5 with the pair
-    arithmetic; 2.8e-6 at 1000 steps)."""
+    (measured between 9.1e-6 and 1.0e-5 across the binary64 and pair
+    evaluations of the records; 2.8e-6 at 1000 steps)."""
     wl = W.sod_1d()
     pr = oracle.Problem(d=1, nx=wl.nx, x0=wl.x0, x1=wl.x1, Qphi=8, Qchi=8, gamma=wl.gamma,
                         tau=wl.tau, dt=wl.dt)
