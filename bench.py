@@ -59,10 +59,10 @@ BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
 # profiles/stage_kernel_mixed_quadrant512.md, valid for the kernel sources
 # whose SHA-256 (over paper_1909_08390_gb300/csrc/*, sorted) is recorded here;
 # reported as null once the sources differ.
-TRAFFIC_SRC_SHA256 = "75abe7901dac9d556c96990c6b918cdafafe18ade0567929e3e6927184f5b5bc"
+TRAFFIC_SRC_SHA256 = "a8cfa107d4a6e549154400cb622b4aa955b2caefe4c14540c0ea13a52dba99bb"
 TRAFFIC_BYTES = {
-    "fp64": {"stage3": 3168712000, "stage4": 2338937000, "final": 1558368000},
-    "mixed": {"stage3": 1563743232, "stage4": 1155023616, "final": 757150720},
+    "fp64": {"stage3": 3169654272, "stage4": 2338732544, "final": 1554452736},
+    "mixed": {"stage3": 528894464, "stage4": 667415296, "final": 418648064},
 }
 
 
