@@ -27,8 +27,7 @@
 
 #include "fdlb.h"
 #include "fdlb_ctx.h"
-#include "fdlb_internal.h"
-#include "fdlb_mp9.cuh"
+#include "fdlb_device.cuh"
 
 namespace fdlb {
 namespace {
@@ -166,16 +165,11 @@ __device__ void mp9_linearize(const double (&v)[9], double (&w)[9]) {
 
 // ---- equilibrium Jacobian ------------------------------------------------
 
-// Per-cell adjoint of F_eq(mom(R)) given Ebar (adjoint of each equilibrium
-// population): returns the per-population adjoint of R through the moments
-// (rbar_n + rbar_j p + rbar_e p^2 for phi, rbar_e for chi) and the adjoint of
-// D+K at fixed moment sums.  m = (n, j, e) of R.
-template <int QP, int QC>
-struct EqAdj {
-  double rn, rj, re;  // adjoints of the moment sums n, j, e
-  double dk;          // adjoint of D + K
-};
-
+// One axis of the equilibrium factors and their u- and T-derivatives
+// (Eq. gExpanded): g_k = sum_l c_lk a_l, dg_k/du = sum_l c_lk l a_{l-1},
+// dg_k/dT = sum_l c_lk l(l-1)/2 a_{l-2}, with c_lk = w_k He_l(p_k)/l!.  The
+// nodes are antisymmetric, so each sum splits into even and odd l and gives
+// the mirror node (Q-1-k) from the same partial sums.
 template <int Q>
 __device__ __forceinline__ void axis_g_derivs(const double* wH, double u, double T, double (&g)[Q],
                                               double (&gu)[Q], double (&gT)[Q]) {
@@ -186,50 +180,112 @@ __device__ __forceinline__ void axis_g_derivs(const double* wH, double u, double
 #pragma unroll
   for (int l = 2; l < Q; ++l) a[l] = fma(u, a[l - 1], ((double)(l - 1) * tm1) * a[l - 2]);
 #pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    double s = 0.0, su = 0.0, sT = 0.0;
+  for (int k = 0; k < (Q + 1) / 2; ++k) {
+    double ge = 0.0, go = 0.0, ue = 0.0, uo = 0.0, te = 0.0, to = 0.0;
 #pragma unroll
     for (int l = 0; l < Q; ++l) {
       const double c = wH[l * kMaxQ + k];
-      s = fma(c, a[l], s);
-      if (l >= 1) su = fma(c * (double)l, a[l - 1], su);
-      if (l >= 2) sT = fma(c * (0.5 * l * (l - 1)), a[l - 2], sT);
+      // even/odd: by the parity of l, which fixes the sign at the mirror node
+      if (l & 1) {
+        go = fma(c, a[l], go);
+        uo = fma(c * (double)l, a[l - 1], uo);
+        if (l >= 2) to = fma(c * (0.5 * l * (l - 1)), a[l - 2], to);
+      } else {
+        ge = fma(c, a[l], ge);
+        if (l >= 1) ue = fma(c * (double)l, a[l - 1], ue);
+        if (l >= 2) te = fma(c * (0.5 * l * (l - 1)), a[l - 2], te);
+      }
     }
-    g[k] = s;
-    gu[k] = su;
-    gT[k] = sT;
+    // parity in p_k: c_{l,Q-1-k} = (-1)^l c_lk
+    g[k] = ge + go;
+    gu[k] = ue + uo;
+    gT[k] = te + to;
+    if (Q - 1 - k != k) {
+      g[Q - 1 - k] = ge - go;
+      gu[Q - 1 - k] = ue - uo;
+      gT[Q - 1 - k] = te - to;
+    }
   }
 }
 
+// A cell's equilibrium at moment sums (n, j, e) with the factor derivatives:
+// phi^eq_k = n g_k(u, T), chi^eq_q = (D+K-d) T n h_q(u, T).
 template <int QP, int QC>
-__device__ __forceinline__ EqAdj<QP, QC> eq_adjoint(const DevParams& p, double n, double j,
-                                                    double e, const double* Ebar) {
-  const double inv_n = 1.0 / n;
-  const double u = j * inv_n;
-  const double T = (e - n * u * u) * inv_n * p.invDK;
+struct EqD {
+  double n, u, T, inv_n;
   double g[QP], gu[QP], gT[QP];
-  axis_g_derivs<QP>(p.wHp, u, T, g, gu, gT);
-  double h[QC], hu[QC], hT[QC];
-  axis_g_derivs<QC>(p.wHc, u, T, h, hu, hT);
+  double h[QC], hu[QC], hT[QC];  // unused (the phi factors serve) when QC == QP
+};
+
+template <int QP, int QC>
+__device__ __forceinline__ void eq_derivs(const DevParams& p, double n, double j, double e,
+                                          EqD<QP, QC>& d) {
+  d.n = n;
+  d.inv_n = 1.0 / n;
+  d.u = j * d.inv_n;
+  d.T = (e - n * d.u * d.u) * d.inv_n * p.invDK;
+  axis_g_derivs<QP>(p.wHp, d.u, d.T, d.g, d.gu, d.gT);
+  if constexpr (QC != QP) axis_g_derivs<QC>(p.wHc, d.u, d.T, d.h, d.hu, d.hT);
+}
+
+template <int QP, int QC>
+__device__ __forceinline__ double eq_hc(const EqD<QP, QC>& d, int q) {
+  if constexpr (QC == QP) return d.g[q];
+  else return d.h[q];
+}
+template <int QP, int QC>
+__device__ __forceinline__ double eq_hu(const EqD<QP, QC>& d, int q) {
+  if constexpr (QC == QP) return d.gu[q];
+  else return d.hu[q];
+}
+template <int QP, int QC>
+__device__ __forceinline__ double eq_hT(const EqD<QP, QC>& d, int q) {
+  if constexpr (QC == QP) return d.gT[q];
+  else return d.hT[q];
+}
+
+template <int QP, int QC>
+__device__ __forceinline__ void eq_values(const DevParams& p, const EqD<QP, QC>& d, double* Feq) {
+#pragma unroll
+  for (int k = 0; k < QP; ++k) Feq[k] = d.n * d.g[k];
+  const double nchi = p.kchi * d.T * d.n;
+#pragma unroll
+  for (int q = 0; q < QC; ++q) Feq[QP + q] = nchi * eq_hc(d, q);
+}
+
+// Per-cell adjoint of F_eq(moments(R)) given Ebar (adjoint of each
+// equilibrium population): the adjoints of the moment sums n, j, e (so that
+// R's populations receive rn + rj p + re p^2 (phi) or re (chi)) and the
+// adjoint of D + K at fixed moment sums.
+struct EqAdj {
+  double rn, rj, re;  // adjoints of the moment sums n, j, e
+  double dk;          // adjoint of D + K
+};
+
+template <int QP, int QC>
+__device__ __forceinline__ EqAdj eq_adjoint(const DevParams& p, const EqD<QP, QC>& d, double e,
+                                            const double* Ebar) {
+  const double n = d.n, u = d.u, T = d.T, inv_n = d.inv_n;
   double nb = 0.0, ub = 0.0, Tb = 0.0, kb = 0.0;
 #pragma unroll
   for (int k = 0; k < QP; ++k) {
     const double eb = Ebar[k];
-    nb = fma(eb, g[k], nb);
-    ub = fma(eb, n * gu[k], ub);
-    Tb = fma(eb, n * gT[k], Tb);
+    nb = fma(eb, d.g[k], nb);
+    ub = fma(eb, n * d.gu[k], ub);
+    Tb = fma(eb, n * d.gT[k], Tb);
   }
   const double kc = p.kchi;
 #pragma unroll
   for (int q = 0; q < QC; ++q) {
     const double eb = Ebar[QP + q];
-    nb = fma(eb, kc * T * h[q], nb);
-    ub = fma(eb, kc * T * n * hu[q], ub);
-    Tb = fma(eb, kc * n * (h[q] + T * hT[q]), Tb);
-    kb = fma(eb, T * n * h[q], kb);
+    const double h = eq_hc(d, q);
+    nb = fma(eb, kc * T * h, nb);
+    ub = fma(eb, kc * T * n * eq_hu(d, q), ub);
+    Tb = fma(eb, kc * n * (h + T * eq_hT(d, q)), Tb);
+    kb = fma(eb, T * n * h, kb);
   }
   // (n, u, T) of (n, j, e): u = j/n, T = (e - j^2/n)/((D+K) n)
-  EqAdj<QP, QC> r;
+  EqAdj r;
   const double DK = p.DK;
   r.rn = nb - ub * u * inv_n + Tb * (2.0 * n * u * u - e) * inv_n * inv_n / DK;
   r.rj = ub * inv_n - Tb * 2.0 * u * inv_n / DK;
@@ -238,22 +294,27 @@ __device__ __forceinline__ EqAdj<QP, QC> eq_adjoint(const DevParams& p, double n
   return r;
 }
 
-// Equilibrium populations of (n, j, e) (as the forward kernels form them).
+// Equilibrium populations only (the forward kernels' even/odd form).
 template <int QP, int QC>
-__device__ __forceinline__ void eq_of_moments(const DevParams& p, double n, double j, double e,
-                                              double* Feq) {
+__device__ __forceinline__ void eq_plain(const DevParams& p, double n, double j, double e,
+                                         double* Feq) {
   const double inv_n = 1.0 / n;
   const double u = j * inv_n;
   const double T = (e - n * u * u) * inv_n * p.invDK;
-  double g[QP], gu[QP], gT[QP];
-  axis_g_derivs<QP>(p.wHp, u, T, g, gu, gT);
-  double h[QC], hu[QC], hT[QC];
-  axis_g_derivs<QC>(p.wHc, u, T, h, hu, hT);
+  double g[QP];
+  axis_g<QP>(p.wHp, u, T, g);
 #pragma unroll
   for (int k = 0; k < QP; ++k) Feq[k] = n * g[k];
   const double nchi = p.kchi * T * n;
+  if constexpr (QC == QP) {
 #pragma unroll
-  for (int q = 0; q < QC; ++q) Feq[QP + q] = nchi * h[q];
+    for (int q = 0; q < QC; ++q) Feq[QP + q] = nchi * g[q];
+  } else {
+    double h[QC];
+    axis_g<QC>(p.wHc, u, T, h);
+#pragma unroll
+    for (int q = 0; q < QC; ++q) Feq[QP + q] = nchi * h[q];
+  }
 }
 
 template <int QP, int QC>
@@ -324,6 +385,9 @@ __device__ __forceinline__ void advect_adjoint(const DevParams& p, const double*
     for (int m = 0; m < 9; ++m) c[m] = fb * w[m];
   }
   __syncthreads();
+  // gather: cell c sits at slot m = c - i + 5 of interface i (p >= 0, i in
+  // [c-3, c+5]) or m = i + 4 - c (p < 0, i in [c-4, c+4]); the clamped ghost
+  // slots of the first and last interfaces add to cells 0 and nx-1
   for (int t = tid; t < P * kTX; t += kNT) {
     const int pop = t / kTX;
     const int lc = t % kTX;
@@ -331,12 +395,24 @@ __device__ __forceinline__ void advect_adjoint(const DevParams& p, const double*
     double acc = 0.0;
     if (cell < nx) {
       const int sgn = p.px[pop] >= 0.0 ? 1 : -1;
-      for (int ii = 0; ii < kNI; ++ii) {
-        const int i = x0 - 5 + ii;
-        if (i < 0 || i > nx) continue;
+      const int ifirst = sgn > 0 ? cell - 3 : cell - 4;
 #pragma unroll
-        for (int m = 0; m < 9; ++m)
-          if (clampi(slot_cell(i, m, sgn), nx) == cell) acc += sm.ctr[pop][ii][m];
+      for (int t9 = 0; t9 < 9; ++t9) {
+        const int i = ifirst + t9;
+        const int m = sgn > 0 ? cell - i + 5 : i + 4 - cell;
+        if (i >= 0 && i <= nx) acc += sm.ctr[pop][i - (x0 - 5)][m];
+      }
+      if (cell == 0 || cell == nx - 1) {
+        // slots whose window cell lies outside [0, nx) and is clamped to `cell`
+        for (int i = (cell == 0 ? 0 : nx - 4); i <= (cell == 0 ? 4 : nx); ++i) {
+          if (i < 0 || i > nx) continue;
+#pragma unroll
+          for (int m = 0; m < 9; ++m) {
+            const int sc = slot_cell(i, m, sgn);
+            if ((cell == 0 && sc < 0) || (cell == nx - 1 && sc > nx - 1))
+              acc += sm.ctr[pop][i - (x0 - 5)][m];
+          }
+        }
       }
     }
     sm.fbar[pop][lc] = acc;
@@ -376,8 +452,10 @@ __global__ void __launch_bounds__(kNT) adj4_kernel(const __grid_constant__ DevPa
     }
     double n, j, e;
     moments_of<QP, QC>(p, F4, n, j, e);  // moments of F4 = moments of R4
+    EqD<QP, QC> d;
+    eq_derivs<QP, QC>(p, n, j, e, d);
     double E4[P];
-    eq_of_moments<QP, QC>(p, n, j, e, E4);
+    eq_values<QP, QC>(p, d, E4);
     const double inv = 1.0 / (1.0 - sc.a44e4);
     double R4b[P];
 #pragma unroll
@@ -388,7 +466,7 @@ __global__ void __launch_bounds__(kNT) adj4_kernel(const __grid_constant__ DevPa
       s_a44 -= F4b[k] * D4;
       s_w4 -= G[k] * D4;
     }
-    const EqAdj<QP, QC> ea = eq_adjoint<QP, QC>(p, n, j, e, Eb);
+    const EqAdj ea = eq_adjoint<QP, QC>(p, d, e, Eb);
     s_dk = ea.dk;
 #pragma unroll
     for (int k = 0; k < P; ++k) {
@@ -416,44 +494,52 @@ __global__ void __launch_bounds__(kNT) adj3_kernel(const __grid_constant__ DevPa
   const int cell = x0 + lc;
   double s[7] = {0, 0, 0, 0, 0, 0, 0};  // a33e3 a43e3 w3e3 k3 k4 kf dk
   if (lc < kTX && cell < p.nx) {
-    double F3[P], Fn[P], G[P], A4b[P], F3b[P];
+    // relaxation of stage 3: F3 = R3 - a33e3 D3, D3 = R3 - F_eq(m(R3))
+    double R3b[P], Eb[P], e;
+    EqD<QP, QC> d;
+    {
+      double F3[P];
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      F3[k] = a.F3s[k * N + cell];
-      Fn[k] = a.Fn[k * N + cell];
-      G[k] = a.Gbar[k * N + cell];
-      A4b[k] = a.A4bar[k * N + cell];
-      F3b[k] = sm.fbar[k][lc];
-    }
-    double n, j, e, n0, j0, e0;
-    moments_of<QP, QC>(p, F3, n, j, e);
-    moments_of<QP, QC>(p, Fn, n0, j0, e0);
-    double E3[P], E0[P];
-    eq_of_moments<QP, QC>(p, n, j, e, E3);
-    eq_of_moments<QP, QC>(p, n0, j0, e0, E0);
-    const double inv = 1.0 / (1.0 - sc.a33e3);
-    double R3b[P], Eb[P];
+      for (int k = 0; k < P; ++k) F3[k] = a.F3s[k * N + cell];
+      double n, j;
+      moments_of<QP, QC>(p, F3, n, j, e);
+      eq_derivs<QP, QC>(p, n, j, e, d);
+      double E3[P];
+      eq_values<QP, QC>(p, d, E3);
+      const double inv = 1.0 / (1.0 - sc.a33e3);
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      const double D3 = (F3[k] - E3[k]) * inv;
-      R3b[k] = (1.0 - sc.a33e3) * F3b[k] - sc.a43e3 * A4b[k] - sc.w3e3 * G[k];
-      Eb[k] = sc.a33e3 * F3b[k] + sc.a43e3 * A4b[k] + sc.w3e3 * G[k];
-      s[0] -= F3b[k] * D3;
-      s[1] -= A4b[k] * D3;
-      s[2] -= G[k] * D3;
+      for (int k = 0; k < P; ++k) {
+        const double D3 = (F3[k] - E3[k]) * inv;
+        const double f3b = sm.fbar[k][lc], a4b = a.A4bar[k * N + cell], g = a.Gbar[k * N + cell];
+        R3b[k] = (1.0 - sc.a33e3) * f3b - sc.a43e3 * a4b - sc.w3e3 * g;
+        Eb[k] = sc.a33e3 * f3b + sc.a43e3 * a4b + sc.w3e3 * g;
+        s[0] -= f3b * D3;
+        s[1] -= a4b * D3;
+        s[2] -= g * D3;
+      }
     }
-    const EqAdj<QP, QC> ea = eq_adjoint<QP, QC>(p, n, j, e, Eb);
+    const EqAdj ea = eq_adjoint<QP, QC>(p, d, e, Eb);
     s[6] = ea.dk;
+    // explicit part R3 = F - k3 D - at32 X2, A4 and A_fin: adjoints of F, D, X2
+    double Fn[P], E0[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) Fn[k] = a.Fn[k * N + cell];
+    {
+      double n0, j0, e0;
+      moments_of<QP, QC>(p, Fn, n0, j0, e0);
+      eq_plain<QP, QC>(p, n0, j0, e0, E0);
+    }
 #pragma unroll
     for (int k = 0; k < P; ++k) {
       const double rb = R3b[k] + (k < QP ? fma(p.p2[k], ea.re, fma(p.px[k], ea.rj, ea.rn)) : ea.re);
+      const double a4b = a.A4bar[k * N + cell], g = a.Gbar[k * N + cell];
       const double D = Fn[k] - E0[k];
       s[3] -= rb * D;
-      s[4] -= A4b[k] * D;
-      s[5] -= G[k] * D;
-      a.Fpart[k * N + cell] = rb + A4b[k] + G[k];
-      a.Dbar[k * N + cell] = -sc.k3 * rb - sc.k4 * A4b[k] - sc.kf * G[k];
-      a.X2bar[k * N + cell] = -sc.at32 * rb - sc.at42 * A4b[k] - sc.wt2 * G[k];
+      s[4] -= a4b * D;
+      s[5] -= g * D;
+      a.Fpart[k * N + cell] = rb + a4b + g;
+      a.Dbar[k * N + cell] = -sc.k3 * rb - sc.k4 * a4b - sc.kf * g;
+      a.X2bar[k * N + cell] = -sc.at32 * rb - sc.at42 * a4b - sc.wt2 * g;
     }
   }
   block_add(&a.scal[kBarA33e3], s[0]);
@@ -487,15 +573,17 @@ __global__ void __launch_bounds__(kNT) adj2_kernel(const __grid_constant__ DevPa
     }
     double n0, j0, e0;
     moments_of<QP, QC>(p, Fn, n0, j0, e0);
+    EqD<QP, QC> d;
+    eq_derivs<QP, QC>(p, n0, j0, e0, d);
     double E0[P];
-    eq_of_moments<QP, QC>(p, n0, j0, e0, E0);
+    eq_values<QP, QC>(p, d, E0);
 #pragma unroll
     for (int k = 0; k < P; ++k) {
       Dt[k] = a.Dbar[k * N + cell] + sc.c2 * F2b[k];  // total adjoint of D
       Eb[k] = F2b[k] - Dt[k];                          // F2 = E0 + c2 D, D = F - E0
       s_c2 += F2b[k] * (Fn[k] - E0[k]);
     }
-    const EqAdj<QP, QC> ea = eq_adjoint<QP, QC>(p, n0, j0, e0, Eb);
+    const EqAdj ea = eq_adjoint<QP, QC>(p, d, e0, Eb);
     s_dk = ea.dk;
 #pragma unroll
     for (int k = 0; k < P; ++k) {
