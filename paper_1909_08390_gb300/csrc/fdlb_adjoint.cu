@@ -208,130 +208,12 @@ __device__ __forceinline__ void axis_g_derivs(const double* wH, double u, double
   }
 }
 
-// A cell's equilibrium at moment sums (n, j, e) with the factor derivatives:
-// phi^eq_k = n g_k(u, T), chi^eq_q = (D+K-d) T n h_q(u, T).
-template <int QP, int QC>
-struct EqD {
-  double n, u, T, inv_n;
-  double g[QP], gu[QP], gT[QP];
-  double h[QC], hu[QC], hT[QC];  // unused (the phi factors serve) when QC == QP
-};
-
-template <int QP, int QC>
-__device__ __forceinline__ void eq_derivs(const DevParams& p, double n, double j, double e,
-                                          EqD<QP, QC>& d) {
-  d.n = n;
-  d.inv_n = 1.0 / n;
-  d.u = j * d.inv_n;
-  d.T = (e - n * d.u * d.u) * d.inv_n * p.invDK;
-  axis_g_derivs<QP>(p.wHp, d.u, d.T, d.g, d.gu, d.gT);
-  if constexpr (QC != QP) axis_g_derivs<QC>(p.wHc, d.u, d.T, d.h, d.hu, d.hT);
-}
-
-template <int QP, int QC>
-__device__ __forceinline__ double eq_hc(const EqD<QP, QC>& d, int q) {
-  if constexpr (QC == QP) return d.g[q];
-  else return d.h[q];
-}
-template <int QP, int QC>
-__device__ __forceinline__ double eq_hu(const EqD<QP, QC>& d, int q) {
-  if constexpr (QC == QP) return d.gu[q];
-  else return d.hu[q];
-}
-template <int QP, int QC>
-__device__ __forceinline__ double eq_hT(const EqD<QP, QC>& d, int q) {
-  if constexpr (QC == QP) return d.gT[q];
-  else return d.hT[q];
-}
-
-template <int QP, int QC>
-__device__ __forceinline__ void eq_values(const DevParams& p, const EqD<QP, QC>& d, double* Feq) {
-#pragma unroll
-  for (int k = 0; k < QP; ++k) Feq[k] = d.n * d.g[k];
-  const double nchi = p.kchi * d.T * d.n;
-#pragma unroll
-  for (int q = 0; q < QC; ++q) Feq[QP + q] = nchi * eq_hc(d, q);
-}
-
-// Per-cell adjoint of F_eq(moments(R)) given Ebar (adjoint of each
-// equilibrium population): the adjoints of the moment sums n, j, e (so that
-// R's populations receive rn + rj p + re p^2 (phi) or re (chi)) and the
-// adjoint of D + K at fixed moment sums.
+// Adjoints of a cell's moment sums n, j, e (so that R's populations receive
+// rn + rj p + re p^2 (phi) or re (chi)) and of D + K at fixed moment sums.
 struct EqAdj {
-  double rn, rj, re;  // adjoints of the moment sums n, j, e
-  double dk;          // adjoint of D + K
+  double rn, rj, re;
+  double dk;
 };
-
-template <int QP, int QC>
-__device__ __forceinline__ EqAdj eq_adjoint(const DevParams& p, const EqD<QP, QC>& d, double e,
-                                            const double* Ebar) {
-  const double n = d.n, u = d.u, T = d.T, inv_n = d.inv_n;
-  double nb = 0.0, ub = 0.0, Tb = 0.0, kb = 0.0;
-#pragma unroll
-  for (int k = 0; k < QP; ++k) {
-    const double eb = Ebar[k];
-    nb = fma(eb, d.g[k], nb);
-    ub = fma(eb, n * d.gu[k], ub);
-    Tb = fma(eb, n * d.gT[k], Tb);
-  }
-  const double kc = p.kchi;
-#pragma unroll
-  for (int q = 0; q < QC; ++q) {
-    const double eb = Ebar[QP + q];
-    const double h = eq_hc(d, q);
-    nb = fma(eb, kc * T * h, nb);
-    ub = fma(eb, kc * T * n * eq_hu(d, q), ub);
-    Tb = fma(eb, kc * n * (h + T * eq_hT(d, q)), Tb);
-    kb = fma(eb, T * n * h, kb);
-  }
-  // (n, u, T) of (n, j, e): u = j/n, T = (e - j^2/n)/((D+K) n)
-  EqAdj r;
-  const double DK = p.DK;
-  r.rn = nb - ub * u * inv_n + Tb * (2.0 * n * u * u - e) * inv_n * inv_n / DK;
-  r.rj = ub * inv_n - Tb * 2.0 * u * inv_n / DK;
-  r.re = Tb * inv_n / DK;
-  r.dk = -Tb * T / DK + kb;  // T = (...)/DK and kchi = DK - d
-  return r;
-}
-
-// Equilibrium populations only (the forward kernels' even/odd form).
-template <int QP, int QC>
-__device__ __forceinline__ void eq_plain(const DevParams& p, double n, double j, double e,
-                                         double* Feq) {
-  const double inv_n = 1.0 / n;
-  const double u = j * inv_n;
-  const double T = (e - n * u * u) * inv_n * p.invDK;
-  double g[QP];
-  axis_g<QP>(p.wHp, u, T, g);
-#pragma unroll
-  for (int k = 0; k < QP; ++k) Feq[k] = n * g[k];
-  const double nchi = p.kchi * T * n;
-  if constexpr (QC == QP) {
-#pragma unroll
-    for (int q = 0; q < QC; ++q) Feq[QP + q] = nchi * g[q];
-  } else {
-    double h[QC];
-    axis_g<QC>(p.wHc, u, T, h);
-#pragma unroll
-    for (int q = 0; q < QC; ++q) Feq[QP + q] = nchi * h[q];
-  }
-}
-
-template <int QP, int QC>
-__device__ __forceinline__ void moments_of(const DevParams& p, const double* F, double& n,
-                                           double& j, double& e) {
-  n = 0.0;
-  j = 0.0;
-  e = 0.0;
-#pragma unroll
-  for (int k = 0; k < QP; ++k) {
-    n += F[k];
-    j = fma(p.px[k], F[k], j);
-    e = fma(p.p2[k], F[k], e);
-  }
-#pragma unroll
-  for (int q = 0; q < QC; ++q) e += F[QP + q];
-}
 
 // ---- the three adjoint stage kernels -------------------------------------
 
@@ -427,6 +309,113 @@ __device__ __forceinline__ void block_add(double* dst, double v) {
   if ((threadIdx.x & 31) == 0) atomicAdd(dst, v);
 }
 
+// ---- per-cell phases: 8 threads per cell ---------------------------------
+// The 128 threads of a tile take its 16 cells 8 at a time: sub-thread s of a
+// cell owns populations s and s + 8, evaluates the equilibrium factor and its
+// derivatives of its own nodes, and the cell's sums (moments, equilibrium
+// adjoint) are reduced over the 8 lanes with shuffles.
+constexpr int kSub = 8;
+static_assert(kTX * kSub == kNT, "8 threads per cell");
+
+// sum over the 8 lanes of a cell (aligned groups of 8 within the warp)
+__device__ __forceinline__ double cell_sum(double v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  return v;
+}
+
+// One node's equilibrium factor and its u- and T-derivatives (Eq. gExpanded).
+template <int Q>
+__device__ __forceinline__ void node_derivs(const double* wH, int k, double u, double T, double& g,
+                                            double& gu, double& gT) {
+  double a[Q];
+  a[0] = 1.0;
+  if (Q > 1) a[1] = u;
+  const double tm1 = T - 1.0;
+#pragma unroll
+  for (int l = 2; l < Q; ++l) a[l] = fma(u, a[l - 1], ((double)(l - 1) * tm1) * a[l - 2]);
+  g = 0.0;
+  gu = 0.0;
+  gT = 0.0;
+#pragma unroll
+  for (int l = 0; l < Q; ++l) {
+    const double c = wH[l * kMaxQ + k];
+    g = fma(c, a[l], g);
+    if (l >= 1) gu = fma(c * (double)l, a[l - 1], gu);
+    if (l >= 2) gT = fma(c * (0.5 * l * (l - 1)), a[l - 2], gT);
+  }
+}
+
+// A population's equilibrium and the factors its adjoint needs.
+struct PopEq {
+  double fe;          // the equilibrium population
+  double dn, du, dT;  // its derivatives with respect to n, u, T
+  double dk;          // its derivative with respect to D + K at fixed n, u, T
+};
+
+template <int QP, int QC>
+__device__ __forceinline__ PopEq pop_eq(const DevParams& p, int pop, double n, double u, double T) {
+  PopEq r;
+  double g, gu, gT;
+  if (pop < QP) {
+    node_derivs<QP>(p.wHp, pop, u, T, g, gu, gT);
+    r.fe = n * g;
+    r.dn = g;
+    r.du = n * gu;
+    r.dT = n * gT;
+    r.dk = 0.0;
+  } else {
+    node_derivs<QC>(p.wHc, pop - QP, u, T, g, gu, gT);
+    const double kc = p.kchi;
+    r.fe = kc * T * n * g;
+    r.dn = kc * T * g;
+    r.du = kc * T * n * gu;
+    r.dT = kc * n * (g + T * gT);
+    r.dk = T * n * g;  // chi^eq = (D+K-d) T n h
+  }
+  return r;
+}
+
+// The cell's (n, j, e) from the sub-thread's populations v[0..1].
+template <int QP, int QC>
+__device__ __forceinline__ void cell_moments(const DevParams& p, int sub, const double (&v)[2],
+                                             double& n, double& j, double& e) {
+  n = 0.0;
+  j = 0.0;
+  e = 0.0;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int pop = sub + kSub * r;
+    if (pop >= QP + QC) break;
+    if (pop < QP) {
+      n += v[r];
+      j = fma(p.px[pop], v[r], j);
+      e = fma(p.p2[pop], v[r], e);
+    } else {
+      e += v[r];
+    }
+  }
+  n = cell_sum(n);
+  j = cell_sum(j);
+  e = cell_sum(e);
+}
+
+// Adjoint of (n, j, e) -> (n, u, T), u = j/n, T = (e - j^2/n)/((D+K) n):
+// from the cell's reduced adjoints of n, u, T and of D+K at fixed (n, u, T)
+// to those of the moment sums and of D+K at fixed moment sums.
+__device__ __forceinline__ EqAdj moments_adjoint(const DevParams& p, double n, double u, double T,
+                                                 double e, double nb, double ub, double Tb,
+                                                 double kb) {
+  const double inv_n = 1.0 / n, DK = p.DK;
+  EqAdj r;
+  r.rn = nb - ub * u * inv_n + Tb * (2.0 * n * u * u - e) * inv_n * inv_n / DK;
+  r.rj = ub * inv_n - Tb * 2.0 * u * inv_n / DK;
+  r.re = Tb * inv_n / DK;
+  r.dk = -Tb * T / DK + kb;  // T = (...)/DK and kchi = DK - d
+  return r;
+}
+
 // Stage 4 + final: from Gbar = adjoint of F^{n+1}.
 template <int QP, int QC>
 __global__ void __launch_bounds__(kNT) adj4_kernel(const __grid_constant__ DevParams p,
@@ -439,41 +428,52 @@ __global__ void __launch_bounds__(kNT) adj4_kernel(const __grid_constant__ DevPa
   // X4bar = -wt4 Gbar
   advect_adjoint<QP, QC>(p, a.F4s, x0, sm,
                          [&](int pop, int c) { return -sc.wt4 * a.Gbar[pop * N + c]; });
-  const int lc = threadIdx.x;
+  const int lc = threadIdx.x / kSub, sub = threadIdx.x % kSub;
   const int cell = x0 + lc;
+  const bool live = cell < p.nx;
   double s_a44 = 0.0, s_w4 = 0.0, s_dk = 0.0;
-  if (lc < kTX && cell < p.nx) {
-    double F4[P], Eb[P], G[P], F4b[P];
+  double F4[2] = {0.0, 0.0};
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      F4[k] = a.F4s[k * N + cell];
-      G[k] = a.Gbar[k * N + cell];
-      F4b[k] = sm.fbar[k][lc];
-    }
-    double n, j, e;
-    moments_of<QP, QC>(p, F4, n, j, e);  // moments of F4 = moments of R4
-    EqD<QP, QC> d;
-    eq_derivs<QP, QC>(p, n, j, e, d);
-    double E4[P];
-    eq_values<QP, QC>(p, d, E4);
-    const double inv = 1.0 / (1.0 - sc.a44e4);
-    double R4b[P];
+  for (int r = 0; r < 2; ++r) {
+    const int pop = sub + kSub * r;
+    if (live && pop < P) F4[r] = a.F4s[pop * N + cell];
+  }
+  double n, j, e;
+  cell_moments<QP, QC>(p, sub, F4, n, j, e);  // moments of F4 = moments of R4
+  if (!live) n = 1.0;                         // a harmless dummy cell
+  const double inv_n = 1.0 / n, u = j * inv_n, T = (e - n * u * u) * inv_n * p.invDK;
+  const double inv = 1.0 / (1.0 - sc.a44e4);
+  double R4b[2] = {0.0, 0.0}, G[2] = {0.0, 0.0};
+  PopEq q[2];
+  double nb = 0.0, ub = 0.0, Tb = 0.0, kb = 0.0;
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      const double D4 = (F4[k] - E4[k]) * inv;  // R4 - E4
-      R4b[k] = (1.0 - sc.a44e4) * F4b[k] - sc.w4e4 * G[k];
-      Eb[k] = sc.a44e4 * F4b[k] + sc.w4e4 * G[k];
-      s_a44 -= F4b[k] * D4;
-      s_w4 -= G[k] * D4;
-    }
-    const EqAdj ea = eq_adjoint<QP, QC>(p, d, e, Eb);
-    s_dk = ea.dk;
+  for (int r = 0; r < 2; ++r) {
+    const int pop = sub + kSub * r;
+    if (pop >= P) break;
+    q[r] = pop_eq<QP, QC>(p, pop, n, u, T);
+    if (!live) continue;
+    G[r] = a.Gbar[pop * N + cell];
+    const double f4b = sm.fbar[pop][lc];
+    const double D4 = (F4[r] - q[r].fe) * inv;  // R4 - E4
+    R4b[r] = (1.0 - sc.a44e4) * f4b - sc.w4e4 * G[r];
+    const double eb = sc.a44e4 * f4b + sc.w4e4 * G[r];
+    s_a44 -= f4b * D4;
+    s_w4 -= G[r] * D4;
+    nb = fma(eb, q[r].dn, nb);
+    ub = fma(eb, q[r].du, ub);
+    Tb = fma(eb, q[r].dT, Tb);
+    kb = fma(eb, q[r].dk, kb);
+  }
+  const EqAdj ea = moments_adjoint(p, n, u, T, e, cell_sum(nb), cell_sum(ub), cell_sum(Tb),
+                                   cell_sum(kb));
+  if (sub == 0 && live) s_dk = ea.dk;
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      double rb = R4b[k] + (k < QP ? fma(p.p2[k], ea.re, fma(p.px[k], ea.rj, ea.rn)) : ea.re);
-      a.A4bar[k * N + cell] = rb;
-      a.X3bar[k * N + cell] = -sc.wt3 * G[k] - sc.at43 * rb;
-    }
+  for (int r = 0; r < 2; ++r) {
+    const int pop = sub + kSub * r;
+    if (pop >= P || !live) break;
+    const double rb = R4b[r] + (pop < QP ? fma(p.p2[pop], ea.re, fma(p.px[pop], ea.rj, ea.rn)) : ea.re);
+    a.A4bar[pop * N + cell] = rb;
+    a.X3bar[pop * N + cell] = -sc.wt3 * G[r] - sc.at43 * rb;
   }
   block_add(&a.scal[kBarA44e4], s_a44);
   block_add(&a.scal[kBarW4e4], s_w4);
@@ -490,57 +490,67 @@ __global__ void __launch_bounds__(kNT) adj3_kernel(const __grid_constant__ DevPa
   const int x0 = blockIdx.x * kTX;
   const int64_t N = p.N;
   advect_adjoint<QP, QC>(p, a.F3s, x0, sm, [&](int pop, int c) { return a.X3bar[pop * N + c]; });
-  const int lc = threadIdx.x;
+  const int lc = threadIdx.x / kSub, sub = threadIdx.x % kSub;
   const int cell = x0 + lc;
+  const bool live = cell < p.nx;
   double s[7] = {0, 0, 0, 0, 0, 0, 0};  // a33e3 a43e3 w3e3 k3 k4 kf dk
-  if (lc < kTX && cell < p.nx) {
-    // relaxation of stage 3: F3 = R3 - a33e3 D3, D3 = R3 - F_eq(m(R3))
-    double R3b[P], Eb[P], e;
-    EqD<QP, QC> d;
-    {
-      double F3[P];
+  // relaxation of stage 3: F3 = R3 - a33e3 D3, D3 = R3 - F_eq(m(R3))
+  double F3[2] = {0.0, 0.0}, Fn[2] = {0.0, 0.0};
 #pragma unroll
-      for (int k = 0; k < P; ++k) F3[k] = a.F3s[k * N + cell];
-      double n, j;
-      moments_of<QP, QC>(p, F3, n, j, e);
-      eq_derivs<QP, QC>(p, n, j, e, d);
-      double E3[P];
-      eq_values<QP, QC>(p, d, E3);
-      const double inv = 1.0 / (1.0 - sc.a33e3);
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const double D3 = (F3[k] - E3[k]) * inv;
-        const double f3b = sm.fbar[k][lc], a4b = a.A4bar[k * N + cell], g = a.Gbar[k * N + cell];
-        R3b[k] = (1.0 - sc.a33e3) * f3b - sc.a43e3 * a4b - sc.w3e3 * g;
-        Eb[k] = sc.a33e3 * f3b + sc.a43e3 * a4b + sc.w3e3 * g;
-        s[0] -= f3b * D3;
-        s[1] -= a4b * D3;
-        s[2] -= g * D3;
-      }
+  for (int r = 0; r < 2; ++r) {
+    const int pop = sub + kSub * r;
+    if (live && pop < P) {
+      F3[r] = a.F3s[pop * N + cell];
+      Fn[r] = a.Fn[pop * N + cell];
     }
-    const EqAdj ea = eq_adjoint<QP, QC>(p, d, e, Eb);
-    s[6] = ea.dk;
-    // explicit part R3 = F - k3 D - at32 X2, A4 and A_fin: adjoints of F, D, X2
-    double Fn[P], E0[P];
+  }
+  double n, j, e, n0, j0, e0;
+  cell_moments<QP, QC>(p, sub, F3, n, j, e);
+  cell_moments<QP, QC>(p, sub, Fn, n0, j0, e0);
+  if (!live) n = n0 = 1.0;
+  const double inv_n = 1.0 / n, u = j * inv_n, T = (e - n * u * u) * inv_n * p.invDK;
+  const double inv_n0 = 1.0 / n0, u0 = j0 * inv_n0, T0 = (e0 - n0 * u0 * u0) * inv_n0 * p.invDK;
+  const double inv = 1.0 / (1.0 - sc.a33e3);
+  double R3b[2] = {0.0, 0.0}, A4b[2] = {0.0, 0.0}, G[2] = {0.0, 0.0};
+  double nb = 0.0, ub = 0.0, Tb = 0.0, kb = 0.0;
 #pragma unroll
-    for (int k = 0; k < P; ++k) Fn[k] = a.Fn[k * N + cell];
-    {
-      double n0, j0, e0;
-      moments_of<QP, QC>(p, Fn, n0, j0, e0);
-      eq_plain<QP, QC>(p, n0, j0, e0, E0);
-    }
+  for (int r = 0; r < 2; ++r) {
+    const int pop = sub + kSub * r;
+    if (pop >= P) break;
+    const PopEq q = pop_eq<QP, QC>(p, pop, n, u, T);
+    if (!live) continue;
+    A4b[r] = a.A4bar[pop * N + cell];
+    G[r] = a.Gbar[pop * N + cell];
+    const double f3b = sm.fbar[pop][lc];
+    const double D3 = (F3[r] - q.fe) * inv;
+    R3b[r] = (1.0 - sc.a33e3) * f3b - sc.a43e3 * A4b[r] - sc.w3e3 * G[r];
+    const double eb = sc.a33e3 * f3b + sc.a43e3 * A4b[r] + sc.w3e3 * G[r];
+    s[0] -= f3b * D3;
+    s[1] -= A4b[r] * D3;
+    s[2] -= G[r] * D3;
+    nb = fma(eb, q.dn, nb);
+    ub = fma(eb, q.du, ub);
+    Tb = fma(eb, q.dT, Tb);
+    kb = fma(eb, q.dk, kb);
+  }
+  const EqAdj ea = moments_adjoint(p, n, u, T, e, cell_sum(nb), cell_sum(ub), cell_sum(Tb),
+                                   cell_sum(kb));
+  if (sub == 0 && live) s[6] = ea.dk;
+  // explicit part R3 = F - k3 D - at32 X2, A4 and A_fin: adjoints of F, D, X2
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      const double rb = R3b[k] + (k < QP ? fma(p.p2[k], ea.re, fma(p.px[k], ea.rj, ea.rn)) : ea.re);
-      const double a4b = a.A4bar[k * N + cell], g = a.Gbar[k * N + cell];
-      const double D = Fn[k] - E0[k];
-      s[3] -= rb * D;
-      s[4] -= a4b * D;
-      s[5] -= g * D;
-      a.Fpart[k * N + cell] = rb + a4b + g;
-      a.Dbar[k * N + cell] = -sc.k3 * rb - sc.k4 * a4b - sc.kf * g;
-      a.X2bar[k * N + cell] = -sc.at32 * rb - sc.at42 * a4b - sc.wt2 * g;
-    }
+  for (int r = 0; r < 2; ++r) {
+    const int pop = sub + kSub * r;
+    if (pop >= P) break;
+    const double e0p = pop_eq<QP, QC>(p, pop, n0, u0, T0).fe;
+    if (!live) continue;
+    const double rb = R3b[r] + (pop < QP ? fma(p.p2[pop], ea.re, fma(p.px[pop], ea.rj, ea.rn)) : ea.re);
+    const double D = Fn[r] - e0p;
+    s[3] -= rb * D;
+    s[4] -= A4b[r] * D;
+    s[5] -= G[r] * D;
+    a.Fpart[pop * N + cell] = rb + A4b[r] + G[r];
+    a.Dbar[pop * N + cell] = -sc.k3 * rb - sc.k4 * A4b[r] - sc.kf * G[r];
+    a.X2bar[pop * N + cell] = -sc.at32 * rb - sc.at42 * A4b[r] - sc.wt2 * G[r];
   }
   block_add(&a.scal[kBarA33e3], s[0]);
   block_add(&a.scal[kBarA43e3], s[1]);
@@ -561,35 +571,46 @@ __global__ void __launch_bounds__(kNT) adj2_kernel(const __grid_constant__ DevPa
   const int x0 = blockIdx.x * kTX;
   const int64_t N = p.N;
   advect_adjoint<QP, QC>(p, a.F2s, x0, sm, [&](int pop, int c) { return a.X2bar[pop * N + c]; });
-  const int lc = threadIdx.x;
+  const int lc = threadIdx.x / kSub, sub = threadIdx.x % kSub;
   const int cell = x0 + lc;
+  const bool live = cell < p.nx;
   double s_c2 = 0.0, s_dk = 0.0;
-  if (lc < kTX && cell < p.nx) {
-    double Fn[P], F2b[P], Eb[P], Dt[P];
+  double Fn[2] = {0.0, 0.0};
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      Fn[k] = a.Fn[k * N + cell];
-      F2b[k] = sm.fbar[k][lc];
-    }
-    double n0, j0, e0;
-    moments_of<QP, QC>(p, Fn, n0, j0, e0);
-    EqD<QP, QC> d;
-    eq_derivs<QP, QC>(p, n0, j0, e0, d);
-    double E0[P];
-    eq_values<QP, QC>(p, d, E0);
+  for (int r = 0; r < 2; ++r) {
+    const int pop = sub + kSub * r;
+    if (live && pop < P) Fn[r] = a.Fn[pop * N + cell];
+  }
+  double n0, j0, e0;
+  cell_moments<QP, QC>(p, sub, Fn, n0, j0, e0);
+  if (!live) n0 = 1.0;
+  const double inv_n0 = 1.0 / n0, u0 = j0 * inv_n0, T0 = (e0 - n0 * u0 * u0) * inv_n0 * p.invDK;
+  double Dt[2] = {0.0, 0.0};
+  double nb = 0.0, ub = 0.0, Tb = 0.0, kb = 0.0;
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      Dt[k] = a.Dbar[k * N + cell] + sc.c2 * F2b[k];  // total adjoint of D
-      Eb[k] = F2b[k] - Dt[k];                          // F2 = E0 + c2 D, D = F - E0
-      s_c2 += F2b[k] * (Fn[k] - E0[k]);
-    }
-    const EqAdj ea = eq_adjoint<QP, QC>(p, d, e0, Eb);
-    s_dk = ea.dk;
+  for (int r = 0; r < 2; ++r) {
+    const int pop = sub + kSub * r;
+    if (pop >= P) break;
+    const PopEq q = pop_eq<QP, QC>(p, pop, n0, u0, T0);
+    if (!live) continue;
+    const double f2b = sm.fbar[pop][lc];
+    Dt[r] = a.Dbar[pop * N + cell] + sc.c2 * f2b;  // total adjoint of D
+    const double eb = f2b - Dt[r];                  // F2 = E0 + c2 D, D = F - E0
+    s_c2 += f2b * (Fn[r] - q.fe);
+    nb = fma(eb, q.dn, nb);
+    ub = fma(eb, q.du, ub);
+    Tb = fma(eb, q.dT, Tb);
+    kb = fma(eb, q.dk, kb);
+  }
+  const EqAdj ea = moments_adjoint(p, n0, u0, T0, e0, cell_sum(nb), cell_sum(ub), cell_sum(Tb),
+                                   cell_sum(kb));
+  if (sub == 0 && live) s_dk = ea.dk;
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-      const double rb = k < QP ? fma(p.p2[k], ea.re, fma(p.px[k], ea.rj, ea.rn)) : ea.re;
-      a.Gnew[k * N + cell] = a.Fpart[k * N + cell] + Dt[k] + rb;
-    }
+  for (int r = 0; r < 2; ++r) {
+    const int pop = sub + kSub * r;
+    if (pop >= P || !live) break;
+    const double rb = pop < QP ? fma(p.p2[pop], ea.re, fma(p.px[pop], ea.rj, ea.rn)) : ea.re;
+    a.Gnew[pop * N + cell] = a.Fpart[pop * N + cell] + Dt[r] + rb;
   }
   block_add(&a.scal[kBarC2], s_c2);
   block_add(&a.scal[kBarDK], s_dk);

@@ -41,6 +41,34 @@ template <>
 struct TileCfg<1, 2> {
   static constexpr int TX = 255, TY = 1, NT = 128, G = 8, SEG = 16;
 };
+// 1-D: 15 and 31 cells, 16 populations per group, 64 threads: short single
+// problems, so that their tiles still spread over the SMs.
+template <>
+struct TileCfg<1, 3> {
+  static constexpr int TX = 15, TY = 1, NT = 64, G = 16, SEG = 4;
+};
+template <>
+struct TileCfg<1, 4> {
+  static constexpr int TX = 31, TY = 1, NT = 64, G = 16, SEG = 8;
+};
+
+// Tile shape of a single 1-D problem of nx cells: the largest tile that
+// still gives about one tile per SM of GB300 (152), down to 15 cells.
+inline int single_1d_variant(int64_t nx) {
+  if (nx >= 127 * 152) return 0;
+  if (nx >= 63 * 152) return 1;
+  if (nx >= 31 * 152) return 4;
+  return 3;
+}
+inline int tile_cells_1d(int variant) {
+  switch (variant) {
+    case 1: return TileCfg<1, 1>::TX;
+    case 2: return TileCfg<1, 2>::TX;
+    case 3: return TileCfg<1, 3>::TX;
+    case 4: return TileCfg<1, 4>::TX;
+    default: return TileCfg<1, 0>::TX;
+  }
+}
 
 // Shared memory of one tile: the advected populations of a group on tile +
 // halo, and the interface values along x and y.

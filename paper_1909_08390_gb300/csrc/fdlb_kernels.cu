@@ -195,13 +195,13 @@ __device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, i
 }
 
 // One tile per CTA, the grid covering one problem.
-template <int DIM, int QP, int QC, int STAGE, typename S>
-__global__ void __launch_bounds__(TileCfg<DIM>::NT)
+template <int DIM, int QP, int QC, int STAGE, typename S, int VAR = 0>
+__global__ void __launch_bounds__(TileCfg<DIM, VAR>::NT)
     stage_kernel(const __grid_constant__ DevParams p) {
-  __shared__ TileSmem<DIM, S, 0> sm;
+  __shared__ TileSmem<DIM, S, VAR> sm;
   const Geo geo{p.nx, p.ny, 0, p.kchi, p.invDK, p.dtdx, p.dtdy, -1};
-  stage_tile<DIM, QP, QC, STAGE, S, 0>(p, geo, blockIdx.x * TileCfg<DIM>::TX,
-                                       blockIdx.y * TileCfg<DIM>::TY, sm);
+  stage_tile<DIM, QP, QC, STAGE, S, VAR>(p, geo, blockIdx.x * TileCfg<DIM, VAR>::TX,
+                                         blockIdx.y * TileCfg<DIM, VAR>::TY, sm);
 }
 
 // Batches of 1-D problems: a persistent grid walks the tile work list of all
@@ -302,17 +302,31 @@ __global__ void moments_kernel(const __grid_constant__ DevParams p, double* __re
   T[c] = TT;
 }
 
-template <int DIM, int QP, int QC, typename S>
-int launch_stage_ts(const DevParams& p, int stage, cudaStream_t s) {
-  using C = TileCfg<DIM>;
+template <int DIM, int QP, int QC, typename S, int VAR>
+int launch_stage_tsv(const DevParams& p, int stage, cudaStream_t s) {
+  using C = TileCfg<DIM, VAR>;
   dim3 grid((p.nx + C::TX - 1) / C::TX, DIM == 2 ? (p.ny + C::TY - 1) / C::TY : 1);
   switch (stage) {
-    case kPrep: stage_kernel<DIM, QP, QC, kPrep, S><<<grid, C::NT, 0, s>>>(p); break;
-    case kStage3: stage_kernel<DIM, QP, QC, kStage3, S><<<grid, C::NT, 0, s>>>(p); break;
-    case kStage4: stage_kernel<DIM, QP, QC, kStage4, S><<<grid, C::NT, 0, s>>>(p); break;
-    default: stage_kernel<DIM, QP, QC, kFinal, S><<<grid, C::NT, 0, s>>>(p); break;
+    case kPrep: stage_kernel<DIM, QP, QC, kPrep, S, VAR><<<grid, C::NT, 0, s>>>(p); break;
+    case kStage3: stage_kernel<DIM, QP, QC, kStage3, S, VAR><<<grid, C::NT, 0, s>>>(p); break;
+    case kStage4: stage_kernel<DIM, QP, QC, kStage4, S, VAR><<<grid, C::NT, 0, s>>>(p); break;
+    default: stage_kernel<DIM, QP, QC, kFinal, S, VAR><<<grid, C::NT, 0, s>>>(p); break;
   }
   return (int)cudaGetLastError();
+}
+
+// 1-D problems pick their tile shape by length (single_1d_variant).
+template <int DIM, int QP, int QC, typename S>
+int launch_stage_ts(const DevParams& p, int stage, cudaStream_t s) {
+  if constexpr (DIM == 1) {
+    switch (single_1d_variant(p.nx)) {
+      case 1: return launch_stage_tsv<1, QP, QC, S, 1>(p, stage, s);
+      case 3: return launch_stage_tsv<1, QP, QC, S, 3>(p, stage, s);
+      case 4: return launch_stage_tsv<1, QP, QC, S, 4>(p, stage, s);
+      default: return launch_stage_tsv<1, QP, QC, S, 0>(p, stage, s);
+    }
+  }
+  return launch_stage_tsv<DIM, QP, QC, S, 0>(p, stage, s);
 }
 
 template <int DIM, int QP, int QC>

@@ -450,14 +450,14 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
     if (valid[k]) finish_cell<DIM, QP, QC>(p, kchi_df, invDK_df, geo.prob, mom[k], rout, cell[k]);
 }
 
-template <int DIM, int QP, int QC, int STAGE>
-__global__ void __launch_bounds__(TileCfg<DIM>::NT, DIM == 2 ? 4 : 8)
+template <int DIM, int QP, int QC, int STAGE, int VAR = 0>
+__global__ void __launch_bounds__(TileCfg<DIM, VAR>::NT, DIM == 2 ? 4 : (TileCfg<DIM, VAR>::NT >= 128 ? 5 : 8))
     mixed_stage_kernel(const __grid_constant__ DevParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  auto& sm = *reinterpret_cast<MixSmem<DIM, QP, QC, 0>*>(smraw);
+  auto& sm = *reinterpret_cast<MixSmem<DIM, QP, QC, VAR>*>(smraw);
   const Geo geo{p.nx, p.ny, 0, p.kchi, p.invDK, p.dtdx, p.dtdy, -1};
-  mixed_tile<DIM, QP, QC, STAGE, 0>(p, geo, blockIdx.x * TileCfg<DIM>::TX,
-                                    blockIdx.y * TileCfg<DIM>::TY, sm);
+  mixed_tile<DIM, QP, QC, STAGE, VAR>(p, geo, blockIdx.x * TileCfg<DIM, VAR>::TX,
+                                      blockIdx.y * TileCfg<DIM, VAR>::TY, sm);
 }
 
 template <int QP, int QC, int STAGE, int VAR>
@@ -536,23 +536,37 @@ int setup_batch_v() {
   return (int)e;
 }
 
+template <int DIM, int QP, int QC, int VAR>
+int launch_tv(const DevParams& p, int stage, cudaStream_t s) {
+  using C = TileCfg<DIM, VAR>;
+  const dim3 grid((p.nx + C::TX - 1) / C::TX, DIM == 2 ? (p.ny + C::TY - 1) / C::TY : 1);
+  const size_t b = sizeof(MixSmem<DIM, QP, QC, VAR>);
+  switch (stage) {
+    case kStage3: mixed_stage_kernel<DIM, QP, QC, kStage3, VAR><<<grid, C::NT, b, s>>>(p); break;
+    case kStage4: mixed_stage_kernel<DIM, QP, QC, kStage4, VAR><<<grid, C::NT, b, s>>>(p); break;
+    default: mixed_stage_kernel<DIM, QP, QC, kFinal, VAR><<<grid, C::NT, b, s>>>(p); break;
+  }
+  return (int)cudaGetLastError();
+}
+
 template <int DIM, int QP, int QC>
 int launch_t(const DevParams& p, int stage, cudaStream_t s) {
-  using C = TileCfg<DIM>;
   if (stage == kPrep) {
     const int nt = 128;
     const int64_t nb = (p.N + nt - 1) / nt;
     mixed_prep_kernel<DIM, QP, QC><<<(unsigned)nb, nt, 0, s>>>(p);
     return (int)cudaGetLastError();
   }
-  const dim3 grid((p.nx + C::TX - 1) / C::TX, DIM == 2 ? (p.ny + C::TY - 1) / C::TY : 1);
-  const size_t b = sizeof(MixSmem<DIM, QP, QC, 0>);
-  switch (stage) {
-    case kStage3: mixed_stage_kernel<DIM, QP, QC, kStage3><<<grid, C::NT, b, s>>>(p); break;
-    case kStage4: mixed_stage_kernel<DIM, QP, QC, kStage4><<<grid, C::NT, b, s>>>(p); break;
-    default: mixed_stage_kernel<DIM, QP, QC, kFinal><<<grid, C::NT, b, s>>>(p); break;
+  if constexpr (DIM == 1) {
+    // 1-D problems pick their tile shape by length (single_1d_variant)
+    switch (single_1d_variant(p.nx)) {
+      case 1: return launch_tv<1, QP, QC, 1>(p, stage, s);
+      case 3: return launch_tv<1, QP, QC, 3>(p, stage, s);
+      case 4: return launch_tv<1, QP, QC, 4>(p, stage, s);
+      default: return launch_tv<1, QP, QC, 0>(p, stage, s);
+    }
   }
-  return (int)cudaGetLastError();
+  return launch_tv<DIM, QP, QC, 0>(p, stage, s);
 }
 
 template <int QP, int QC, int VAR>
