@@ -177,6 +177,17 @@ def _max_over_ranks(world, value: float) -> float:
     return float(t.item())
 
 
+def _sum_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def cpu_baseline_sample(steps: int = 1, rows: int = 64):
     """Oracle timing on the first `rows` rows of the workload (FP64, host)."""
     from oracle import oracle as O
@@ -435,8 +446,12 @@ def run_ours(args, world, rank, local):
     # gamma, binary32 storage, autotuned tiles, graph replay) against the
     # single-problem binary64 path run problem by problem
     batched = None
-    if not args.no_batched and world == 1:
-        probs = W.batched_problems(0)
+    if not args.no_batched:
+        # the problems are independent: under torchrun each rank takes its own
+        # share (no collective on the data path; max of the ranks' times)
+        allp = W.batched_problems(0)
+        total_cells = sum(q["nx"] for q in allp)
+        probs = [allp[i] for i in W.shard_problems([q["nx"] for q in allp], rank, world)]
         bnx = [q["nx"] for q in probs]
         bgm = [q["gamma"] for q in probs]
         bst = np.array([q["states"] for q in probs])
@@ -446,17 +461,19 @@ def run_ours(args, world, rank, local):
         bs.step(args.warmup, allow_unstable=True)
         torch.cuda.synchronize()
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _barrier(world)
         b0.record(stream)
         bs.step(args.steps, allow_unstable=True)
         b1.record(stream)
         torch.cuda.synchronize()
-        b_ms = b0.elapsed_time(b1)
-        b_units = bs.P * bs.N * args.steps
+        b_ms = _max_over_ranks(world, b0.elapsed_time(b1))
+        b_units = bs.P * total_cells * args.steps  # all ranks' problems
         flags = bs.status()
         bs.close()
         # sequential binary64 single-problem contexts on every 16th problem
+        # (one GPU only: the comparison is with the batch on the same GPU)
         seq_ms, seq_cells = 0.0, 0
-        for i in range(0, len(probs), 16):
+        for i in range(0, len(probs) if world == 1 else 0, 16):
             with fdlb.Solver(d=1, nx=bnx[i], x0=-0.5, x1=0.5, Qphi=8, Qchi=8, gamma=bgm[i],
                              tau=1e-6, dt=2e-5, stream=stream) as one:
                 one.init_riemann(bst[i], 0.0)
@@ -475,18 +492,20 @@ def run_ours(args, world, rank, local):
                 torch.cuda.synchronize()
                 seq_ms += s0.elapsed_time(s1)
                 seq_cells += bnx[i]
-        seq_ms_all = seq_ms * (sum(bnx) / seq_cells)
+        seq_ms_all = seq_ms * (total_cells / seq_cells) if seq_cells else None
         batched = {
             "workload": "512 two-state 1-D problems, Nx ~ U[256,4096] (total %d cells), gamma ~ "
-                        "U[1.1,5/3], Q=8 (16 populations), tau=1e-6, dt=2e-5" % sum(bnx),
+                        "U[1.1,5/3], Q=8 (16 populations), tau=1e-6, dt=2e-5" % total_cells,
+            "scaling": "strong (the 512 problems dealt out over the ranks)",
+            "problems_per_rank": len(probs),
             "value": b_units / (b_ms * 1e-3), "unit": UNIT,
             "dtype": "f32 storage/advection, f64-accurate moments",
             "ms_per_step": b_ms / args.steps,
-            "sequential_fp64_ms_per_step": seq_ms_all / args.steps,
-            "speedup_vs_sequential_fp64": seq_ms_all / b_ms,
+            "sequential_fp64_ms_per_step": seq_ms_all / args.steps if seq_ms_all else None,
+            "speedup_vs_sequential_fp64": seq_ms_all / b_ms if seq_ms_all else None,
             "sequential_sample": "every 16th problem (32), scaled by cell count",
             "tiling": {"cells_per_tile": [127, 63, 255][variant], "ctas_per_sm": ctas},
-            "unstable_members": int((flags != 0).sum()),
+            "unstable_members": int(_sum_over_ranks(world, float((flags != 0).sum()))),
             "gpu_launches": 3 * args.steps,
         }
 

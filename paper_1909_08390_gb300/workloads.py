@@ -155,6 +155,20 @@ def batched_problems(seed: int = 0, nprob: int = 512, nx_lo: int = 256, nx_hi: i
     return probs
 
 
+def shard_problems(nx, rank: int, world: int):
+    """Indices of the independent problems rank `rank` of `world` runs: the
+    problems sorted by length and dealt out in a serpentine (0..w-1, w-1..0,
+    ...) so every rank gets a similar cell count.  No problem is shared and
+    none is left out."""
+    order = sorted(range(len(nx)), key=lambda i: (-nx[i], i))
+    mine = []
+    for pos, i in enumerate(order):
+        lap, r = divmod(pos, world)
+        if (r if lap % 2 == 0 else world - 1 - r) == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
 def smooth_fields_1d(nx: int, seed: int = 0, amp: float = 0.1, periodic: bool = True):
     """Smooth periodic (rho, u, T) built from a few low Fourier modes."""
     rng = np.random.default_rng(seed)
