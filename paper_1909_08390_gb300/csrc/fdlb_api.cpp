@@ -275,6 +275,10 @@ int params_for(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double t
   if (g.nx < 1 || ny < 1 || g.nx > (1 << 30) || ny > (1 << 30))
     return set_err(nullptr, FDLB_EINVAL, "bad cell counts nx=%lld ny=%lld", (long long)g.nx,
                    (long long)g.ny);
+  // the kernels index cells with 32-bit offsets
+  if (g.nx * ny >= ((int64_t)1 << 31))
+    return set_err(nullptr, FDLB_EINVAL, "nx*ny = %lld cells: at most 2^31 - 1",
+                   (long long)(g.nx * ny));
   if (!(g.x1 > g.x0) || (g.d == 2 && !(g.y1 > g.y0)))
     return set_err(nullptr, FDLB_EINVAL, "empty domain");
   if (g.bc != FDLB_BC_OUTLET && g.bc != FDLB_BC_PERIODIC)
@@ -379,6 +383,10 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
   if (g.nx < 1 || ny < 1 || g.nx > (1 << 30) || ny > (1 << 30))
     return set_err(nullptr, FDLB_EINVAL, "bad cell counts nx=%lld ny=%lld", (long long)g.nx,
                    (long long)g.ny);
+  // the kernels index cells with 32-bit offsets
+  if (g.nx * ny >= ((int64_t)1 << 31))
+    return set_err(nullptr, FDLB_EINVAL, "nx*ny = %lld cells: at most 2^31 - 1",
+                   (long long)(g.nx * ny));
   if (!(g.x1 > g.x0) || (g.d == 2 && !(g.y1 > g.y0)))
     return set_err(nullptr, FDLB_EINVAL, "empty domain");
   if (g.bc != FDLB_BC_OUTLET && g.bc != FDLB_BC_PERIODIC)
@@ -742,6 +750,9 @@ int fdlb_create_batch(int nprob, const int64_t* nx, const double* gamma, double 
     b.dx = dx;
     b.xsplit = 0.5 * (x0 + x1);
     total += nx[i];
+    // the kernels index cells with 32-bit offsets
+    if (total >= ((int64_t)1 << 31))
+      return set_err(nullptr, FDLB_EINVAL, "batch of more than 2^31 - 1 cells");
   }
   if (total > ((int64_t)1 << 31) / 2) return set_err(nullptr, FDLB_EINVAL, "too many cells");
   fdlb_ctx* c = new (std::nothrow) fdlb_ctx();

@@ -49,6 +49,7 @@ def _grid(**kw):
     (dict(), (8, 8, 1.4, 0.0, 1e-5), fdlb.FDLB_EINVAL),          # tau
     (dict(), (8, 8, 1.4, 1e-6, -1.0), fdlb.FDLB_EINVAL),         # dt
     (dict(nx=400), (8, 8, 1.4, 1e-6, 1e-3), fdlb.FDLB_ECFL),     # 4.14*1e-3*400 > 1
+    (dict(d=2, nx=65536, ny=65536), (8, 8, 1.4, 1e-6, 1e-8), fdlb.FDLB_EINVAL),  # 2^32 cells
 ])
 def test_create_rejects_bad_arguments(lib, kw, args, code):
     out = ctypes.c_void_p()

@@ -222,3 +222,16 @@ def test_invalid_state_reports_unstable(F):
         # a valid state clears the status
         s.init_riemann(W.sod_1d().states, 0.5)
         s.step(2)
+
+
+def test_allocation_failure_reported(F):
+    """A grid whose six population arrays need about 9.8 TB: the device
+    allocation fails and fdlb_create returns FDLB_ENOMEM with no context."""
+    g = F.fdlb_grid(2, 40000, 40000, 0.0, 1.0, 0.0, 1.0, F.FDLB_BC_OUTLET)
+    with pytest.raises(F.FdlbError) as ei:
+        F.fdlb_create(g, 8, 8, 1.4, 1e-6, 1e-7, None, F.FDLB_FP64, None)
+    assert ei.value.code == F.FDLB_ENOMEM
+    # the library and the device stay usable
+    with F.Solver(d=1, nx=64) as s:
+        s.init_riemann(W.sod_1d().states, 0.0)
+        s.step(2)
