@@ -304,6 +304,26 @@ struct CoefS {
         a43e3((S)c.a43e3), w3e3((S)c.w3e3), a44e4((S)c.a44e4), w4e4((S)c.w4e4), c2((S)c.c2) {}
 };
 
+// Asynchronous global -> shared copies of one element (4 or 8 bytes): the
+// prefetch of the next population group.  A thread that copies elements
+// waits on its own copies before reading them, or before a barrier after
+// which other threads read them.
+template <typename S>
+__device__ __forceinline__ void cp_async(S* smem, const S* gmem) {
+  static_assert(sizeof(S) == 4 || sizeof(S) == 8, "4- or 8-byte elements");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(S) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Lattices of the batch kernels (1-D).
 #define FDLB_BATCH_LATTICES(X) \
   X(8, 8)                      \

@@ -81,22 +81,43 @@ __device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, i
     const int tg = tid / (NLINE * NSEG);
     const int tline = (tid / NSEG) % NLINE;
     const int tseg = tid % NSEG;
-    for (int g0 = 0; g0 < L::P; g0 += G) {
-      // ---- stage the advected populations of this group on tile + halo
-      for (int i = tid; i < G * SY * SX; i += NT) {
-        const int g = i / (SY * SX);
-        const int r = (i / SX) % SY;
-        const int cidx = i % SX;
-        const int pop = g0 + g;
-        S v = 0;
-        if (pop < L::P && cidx < TX + 2 * H) {
-          const int gx = wrap_or_clamp(x0 - H + cidx, geo.nx, p.bc);
-          const int gy = (DIM == 2) ? wrap_or_clamp(y0 - H + r, geo.ny, p.bc) : 0;
-          v = adv[pop * N + geo.base + (int64_t)gy * geo.nx + gx];
-        }
-        tile[g][r][cidx] = v;
+    // this thread's staged cells (tile offset, cell offset from geo.base or
+    // -1): ghosts by index clamp or wrap; the 2-D halo corners feed no line
+    constexpr int SXH = TX + 2 * H;
+    constexpr int NST = SY * SXH;
+    constexpr int J = (NST + NT - 1) / NT;
+    int soff[J], goff[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+      const int e = tid + j * NT;
+      const int r = e / SXH, c = e % SXH;
+      soff[j] = r * SX + c;
+      goff[j] = -1;
+      const bool corner = DIM == 2 && (r < H || r >= H + TY) && (c < H || c >= H + TX);
+      if (e < NST && !corner) {
+        const int gx = wrap_or_clamp(x0 - H + c, geo.nx, p.bc);
+        const int gy = (DIM == 2) ? wrap_or_clamp(y0 - H + r, geo.ny, p.bc) : 0;
+        goff[j] = gy * geo.nx + gx;
       }
-      __syncthreads();
+    }
+    // the group's advected populations on tile + halo, copied asynchronously;
+    // the next group's copies run during this group's pass 1
+    auto prefetch = [&](int gfirst) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int pop = gfirst + g;
+        if (pop >= L::P) break;
+        const S* __restrict__ src = adv + (int64_t)pop * N + geo.base;
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+          if (goff[j] >= 0) cp_async(&tile[g][0][0] + soff[j], src + goff[j]);
+      }
+      cp_async_commit();
+    };
+    prefetch(0);
+    for (int g0 = 0; g0 < L::P; g0 += G) {
+      cp_async_wait_all();
+      __syncthreads();  // the group's tile is in; the previous pass 1 is done
       // ---- every interface value once, marching upwind -> downwind
       {
         const int pop = g0 + tg;
@@ -118,7 +139,8 @@ __device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, i
         S* out = xline ? &hx[tg][r][first] : &hy[tg][c][first];
         mp9_march<SEG>(base, sgn * stride, out, sgn);
       }
-      __syncthreads();
+      __syncthreads();  // the march is done with the tile
+      if (g0 + G < L::P) prefetch(g0 + G);
       // ---- flux difference, explicit part, moments (pass 1)
 #pragma unroll
       for (int k = 0; k < CPT; ++k) {
@@ -151,8 +173,8 @@ __device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, i
           accumulate<DIM, QP, QC>(p, mom[k], pop, R);
         }
       }
-      __syncthreads();
     }
+    __syncthreads();  // every thread past its last use of hx, hy
   }
 
   // ---- pass 2: equilibrium of the moments and closed-form relaxation

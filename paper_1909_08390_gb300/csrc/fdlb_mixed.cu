@@ -183,18 +183,6 @@ __device__ __forceinline__ void finish_cell(const DevParams& p, DF kchi, DF invD
   write_record<DIM, QP, QC>(p, kchi, n, ux, uy, T, rec, cell, p.N);
 }
 
-// Asynchronous 4-byte global -> shared copies (prefetch of the next group).
-__device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
-
 // Record prefetch plan of a population group, for lattices with Qchi = Qphi
 // whose groups align with rows of the velocity grid ((8, 8) with groups of 4
 // in 2-D; groups of 8 or 16 in 1-D).  Slot s of the group's buffer holds one
@@ -328,7 +316,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
       const float* __restrict__ src = adv + (int64_t)pop * N + geo.base;
 #pragma unroll
       for (int j = 0; j < J; ++j)
-        if (goff[j] >= 0) cp_async4(&sm.raw[g][tid + j * NT], src + goff[j]);
+        if (goff[j] >= 0) cp_async(&sm.raw[g][tid + j * NT], src + goff[j]);
     }
     if constexpr (GR::kOn) {
 #pragma unroll
@@ -338,7 +326,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
         const float* __restrict__ src = rbase + (int64_t)comp * N;
 #pragma unroll
         for (int j = 0; j < J; ++j)
-          if (goff[j] >= 0) cp_async4(&sm.rbuf[sl][tid + j * NT], src + goff[j]);
+          if (goff[j] >= 0) cp_async(&sm.rbuf[sl][tid + j * NT], src + goff[j]);
       }
     }
     cp_async_commit();

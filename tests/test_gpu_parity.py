@@ -225,9 +225,10 @@ def test_invalid_state_reports_unstable(F):
 
 
 def test_allocation_failure_reported(F):
-    """A grid whose six population arrays need about 9.8 TB: the device
-    allocation fails and fdlb_create returns FDLB_ENOMEM with no context."""
-    g = F.fdlb_grid(2, 40000, 40000, 0.0, 1.0, 0.0, 1.0, F.FDLB_BC_OUTLET)
+    """A 20000^2 grid (4e8 cells, below the 2^30-cell limit) whose six
+    binary64 population arrays need about 2.5 TB: the device allocation fails
+    and fdlb_create returns FDLB_ENOMEM with no context."""
+    g = F.fdlb_grid(2, 20000, 20000, 0.0, 1.0, 0.0, 1.0, F.FDLB_BC_OUTLET)
     with pytest.raises(F.FdlbError) as ei:
         F.fdlb_create(g, 8, 8, 1.4, 1e-6, 1e-7, None, F.FDLB_FP64, None)
     assert ei.value.code == F.FDLB_ENOMEM
