@@ -150,10 +150,14 @@ __device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, i
         for (int g = 0; g < G; ++g) {
           const int pop = g0 + g;
           if (pop >= L::P) break;
-          // X = dt * (p . grad F) = dt p_x (Fhat_{x+1/2} - Fhat_{x-1/2})/dx + (y)
-          S X = (S)(geo.dtdx * p.px[pop]) * (hx[g][ly][lx + 1] - hx[g][ly][lx]);
-          if constexpr (DIM == 2)
-            X = sfma((S)(geo.dtdy * p.py[pop]), hy[g][lx][ly + 1] - hy[g][lx][ly], X);
+          // X = dt * (p . grad F) = dt p_x (Fhat_{x+1/2} - Fhat_{x-1/2})/dx + (y);
+          // single problems use the host's dt p/dx (the same product)
+          const double cxv = geo.prob < 0 ? p.cx[pop] : geo.dtdx * p.px[pop];
+          S X = (S)cxv * (hx[g][ly][lx + 1] - hx[g][ly][lx]);
+          if constexpr (DIM == 2) {
+            const double cyv = geo.prob < 0 ? p.cy[pop] : geo.dtdy * p.py[pop];
+            X = sfma((S)cyv, hy[g][lx][ly + 1] - hy[g][lx][ly], X);
+          }
           const int64_t e = pop * N + cell[k];
           S R;
           if (STAGE == kStage3) {
