@@ -42,6 +42,17 @@ UNIT = "cell-velocity updates/s"
 # (stage 3: 12 + 4 + 8; stage 4: 4 + 4 + 6; final: 2 + 4 + 4).  The limited
 # MP branch, divisions and per-cell equilibrium factors are not counted.
 FLOPS_PER_POP = {"stage3": 48 + 5 + 24, "stage4": 48 + 5 + 14, "final": 48 + 5 + 10}
+# The kernels are bound by GB300's binary64 pipe, which executes one add,
+# multiply or fused multiply-add per lane slot (2 slots per SM and clock), so
+# the roofline counts binary64 operations, not flops.  Algorithmic operations
+# per population and launch: one MP-9 interface value per axis (x and y), 15
+# each (the new difference, the 8-term stencil, the curvature, the two DM
+# candidates, the MD and LC bounds, the clamped result); the flux difference 4
+# (two differences, a multiply, an fma); then the stage's explicit part,
+# moment sums and relaxation: stage 3 6 + 4 + 5, stage 4 2 + 4 + 4, final
+# 1 + 4 + 3.  The tiles' extra interface per line, the per-cell equilibrium
+# factors and divisions are not counted.
+FP64_OPS_PER_POP = {"stage3": 30 + 4 + 15, "stage4": 30 + 4 + 10, "final": 30 + 4 + 8}
 # Algorithmic HBM bytes per population and launch (binary64): arrays read and
 # written once each by the kernel (stage 3: F2, F, D -> F3, A4, Af; stage 4:
 # F3, A4, Af -> A4, Af; final: A4, Af -> F, D, F2).
@@ -85,6 +96,7 @@ def _traffic(kind, stage):
 # binary64 peak: 152 SMs x 2 DFMA lanes/clk/SM (the 1.25 TFLOP/s nominal
 # figure of GB300 at 2070 MHz) x 2 flops x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PEAK_GOPS = 152 * 2 * 2.07e9 / 1e9  # binary64 operations per second
 
 
 def _env_int(name, default):
@@ -383,14 +395,19 @@ def run_ours(args, world, rank, local):
     per_launch_ms = stage_ms[top] / args.steps
     flops = FLOPS_PER_POP[names[top]] * units_per_step
     achieved_tflops = flops / (per_launch_ms * 1e-3) / 1e12
+    ops = FP64_OPS_PER_POP[names[top]] * units_per_step
+    achieved_gops = ops / (per_launch_ms * 1e-3) / 1e9
     hbm_bytes = BYTES_PER_POP[names[top]] * units_per_step
     peaks = _load_peaks()
     roofline = {
         "bound": "alu", "kernel": f"stage_kernel<2,8,8,{names[top]}>",
-        "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-        "frac": achieved_tflops / FP64_PEAK_TFLOPS,
-        "peak_source": "binary64 nominal: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz",
+        "achieved": achieved_gops, "peak": FP64_PEAK_GOPS, "unit": "G binary64 op/s",
+        "frac": achieved_gops / FP64_PEAK_GOPS,
+        "peak_source": "binary64 pipe, nominal: 152 SMs x 2 lanes/clk x 2.07 GHz (1.26 TFLOP/s "
+                       "with FMA = 2); MEASURED_PEAKS.json has no binary64 figure",
         "traffic": _traffic("fp64", names[top]),
+        "algorithmic_ops_per_launch": ops,
+        "achieved_tflops": achieved_tflops, "tflops_frac": achieved_tflops / FP64_PEAK_TFLOPS,
         "algorithmic_flops_per_launch": flops,
         "avg_launch_ms": per_launch_ms,
         "stage_ms_per_step": {n: v / args.steps for n, v in zip(names, stage_ms)},
@@ -468,6 +485,8 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         b_ms = _max_over_ranks(world, b0.elapsed_time(b1))
         b_units = bs.P * total_cells * args.steps  # all ranks' problems
+        b_gbs = ((48 + 3 * 2 * 9 * 4 / 16) * bs.P * total_cells / world
+                 / (b_ms / args.steps * 1e-3) / 1e9)
         flags = bs.status()
         bs.close()
         # sequential binary64 single-problem contexts on every 16th problem
@@ -506,6 +525,14 @@ def run_ours(args, world, rank, local):
             "sequential_sample": "every 16th problem (32), scaled by cell count",
             "tiling": {"cells_per_tile": [127, 63, 255][variant], "ctas_per_sm": ctas},
             "unstable_members": int(_sum_over_ranks(world, float((flags != 0).sum()))),
+            # whole-step algorithmic HBM bytes of the three single-pass kernels:
+            # 12 population arrays of 4 B and, per kernel, one 9-component cell
+            # record read and one written (2 * 9 * 4 / 16 B per population)
+            "roofline": {
+                "bound": "hbm", "scope": "whole step (3 kernels), per GPU",
+                "achieved": b_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": b_gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
             "gpu_launches": 3 * args.steps,
         }
 
