@@ -598,6 +598,50 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def run_mixed_at_scale(args):
+    """The 2048 x 2048 x 128-population run of the mixed path (binary32
+    populations, about 2.1 GB per array) with the benchmark seed's quadrant
+    states for `--scale-steps` steps, timed, and its n, u, v, T error against
+    the same run in binary64 on the GPU.  Not part of the default line (the
+    binary64 run takes about 0.21 s per step)."""
+    import numpy as np
+    import torch
+
+    from paper_1909_08390_gb300 import build as B, fdlb, workloads as W
+    B.build()
+    fdlb.load()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    wl = W.quadrant_2d(W.BENCH_SEED, n=2048)
+    res, ms = {}, {}
+    for name, prec in (("mixed", fdlb.FDLB_MIXED), ("fp64", fdlb.FDLB_FP64)):
+        with fdlb.Solver.from_workload(wl, precision=prec, stream=stream) as s:
+            s.init_riemann(wl.states, 0.5, 0.5)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(args.scale_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms[name] = e0.elapsed_time(e1)
+            res[name] = s.moments()
+    rel = lambda a, b, floor=0.0: float(np.abs(a - b).max() / max(np.abs(b).max(), floor))
+    (mn, mu, mv, mT), (fn, fu, fv, fT) = res["mixed"], res["fp64"]
+    units = 2048 * 2048 * 128 * args.scale_steps
+    print(json.dumps({
+        "workload": "quadrant_2d_s%d 2048x2048, 8x8 velocities (128 pops), gamma=1.4, tau=1e-6, "
+                    "dt=2.5e-5" % W.BENCH_SEED,
+        "steps": args.scale_steps,
+        "mixed": {"ms_per_step": ms["mixed"] / args.scale_steps,
+                  "value": units / (ms["mixed"] * 1e-3), "unit": UNIT},
+        "fp64": {"ms_per_step": ms["fp64"] / args.scale_steps,
+                 "value": units / (ms["fp64"] * 1e-3), "unit": UNIT},
+        "mixed_err_vs_fp64": {"n": rel(mn, fn), "u": rel(mu, fu, 1.0), "v": rel(mv, fv, 1.0),
+                              "T": rel(mT, fT)},
+    }), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -608,9 +652,14 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--scale-steps", type=int, default=0,
+                    help="instead of the benchmark: the 2048^2 mixed run against binary64, "
+                         "this many steps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = _dist_setup()
+    if args.scale_steps > 0:
+        return run_mixed_at_scale(args) if rank == 0 else 0
     if args.impl == "reference":
         return run_reference(args, world, rank)
     return run_ours(args, world, rank, local)
