@@ -70,10 +70,10 @@ BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
 # profiles/stage_kernel_mixed_quadrant512.md, valid for the kernel sources
 # whose SHA-256 (over paper_1909_08390_gb300/csrc/*, sorted) is recorded here;
 # reported as null once the sources differ.
-TRAFFIC_SRC_SHA256 = "a8cfa107d4a6e549154400cb622b4aa955b2caefe4c14540c0ea13a52dba99bb"
+TRAFFIC_SRC_SHA256 = "190d6fa93d055e9deef7d9b3294f9c054d43a36e394d715929679562c24f91ec"
 TRAFFIC_BYTES = {
-    "fp64": {"stage3": 3169654272, "stage4": 2338732544, "final": 1554452736},
-    "mixed": {"stage3": 528894464, "stage4": 667415296, "final": 418648064},
+    "fp64": {"stage3": 3180514816, "stage4": 2332041984, "final": 1563790080},
+    "mixed": {"stage3": 528610560, "stage4": 666187520, "final": 418804480},
 }
 
 
