@@ -599,11 +599,13 @@ def run_ours(args, world, rank, local):
 
 
 def run_mixed_at_scale(args):
-    """The 2048 x 2048 x 128-population run of the mixed path (binary32
-    populations, about 2.1 GB per array) with the benchmark seed's quadrant
-    states for `--scale-steps` steps, timed, and its n, u, v, T error against
-    the same run in binary64 on the GPU.  Not part of the default line (the
-    binary64 run takes about 0.21 s per step)."""
+    """The mixed path (binary32 populations) on the benchmark seed's quadrant
+    problem at `--scale-n`^2 cells x 128 populations (2048: about 2.1 GB per
+    array) for `--scale-steps` steps, timed, with its n, u, v, T difference
+    from the same run in binary64 on the GPU (max-norm and L1, relative).  A
+    third run, binary64 from the initial state rounded to binary32, shows how
+    far the problem itself carries a binary32-sized perturbation.  Not part of
+    the default line (the binary64 run at 2048^2 takes about 0.19 s per step)."""
     import numpy as np
     import torch
 
@@ -612,11 +614,16 @@ def run_mixed_at_scale(args):
     fdlb.load()
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    wl = W.quadrant_2d(W.BENCH_SEED, n=2048)
+    n = args.scale_n
+    wl = W.quadrant_2d(W.BENCH_SEED, n=n)
     res, ms = {}, {}
-    for name, prec in (("mixed", fdlb.FDLB_MIXED), ("fp64", fdlb.FDLB_FP64)):
+    runs = (("mixed", fdlb.FDLB_MIXED, False), ("fp64", fdlb.FDLB_FP64, False),
+            ("fp64_from_binary32_start", fdlb.FDLB_FP64, True))
+    for name, prec, rounded in runs:
         with fdlb.Solver.from_workload(wl, precision=prec, stream=stream) as s:
             s.init_riemann(wl.states, 0.5, 0.5)
+            if rounded:
+                s.set_state(s.state().astype(np.float32).astype(np.float64))
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -625,19 +632,25 @@ def run_mixed_at_scale(args):
             torch.cuda.synchronize()
             ms[name] = e0.elapsed_time(e1)
             res[name] = s.moments()
-    rel = lambda a, b, floor=0.0: float(np.abs(a - b).max() / max(np.abs(b).max(), floor))
-    (mn, mu, mv, mT), (fn, fu, fv, fT) = res["mixed"], res["fp64"]
-    units = 2048 * 2048 * 128 * args.scale_steps
+
+    def diff(a, b):
+        out = {}
+        for k, x, y, floor in zip("nuvT", a, b, (0.0, 1.0, 1.0, 0.0)):
+            out[k] = {"max": float(np.abs(x - y).max() / max(np.abs(y).max(), floor)),
+                      "l1": float(np.abs(x - y).sum() / max(np.abs(y).sum(), floor * y.size))}
+        return out
+
+    units = n * n * 128 * args.scale_steps
     print(json.dumps({
-        "workload": "quadrant_2d_s%d 2048x2048, 8x8 velocities (128 pops), gamma=1.4, tau=1e-6, "
-                    "dt=2.5e-5" % W.BENCH_SEED,
+        "workload": "quadrant_2d_s%d %dx%d, 8x8 velocities (128 pops), gamma=1.4, tau=1e-6, "
+                    "dt=2.5e-5" % (W.BENCH_SEED, n, n),
         "steps": args.scale_steps,
         "mixed": {"ms_per_step": ms["mixed"] / args.scale_steps,
                   "value": units / (ms["mixed"] * 1e-3), "unit": UNIT},
         "fp64": {"ms_per_step": ms["fp64"] / args.scale_steps,
                  "value": units / (ms["fp64"] * 1e-3), "unit": UNIT},
-        "mixed_err_vs_fp64": {"n": rel(mn, fn), "u": rel(mu, fu, 1.0), "v": rel(mv, fv, 1.0),
-                              "T": rel(mT, fT)},
+        "mixed_vs_fp64": diff(res["mixed"], res["fp64"]),
+        "fp64_binary32_start_vs_fp64": diff(res["fp64_from_binary32_start"], res["fp64"]),
     }), flush=True)
     return 0
 
@@ -652,9 +665,10 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--scale-n", type=int, default=2048)
     ap.add_argument("--scale-steps", type=int, default=0,
-                    help="instead of the benchmark: the 2048^2 mixed run against binary64, "
-                         "this many steps")
+                    help="instead of the benchmark: the seeded quadrant problem at "
+                         "--scale-n^2 cells, mixed against binary64, this many steps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = _dist_setup()
