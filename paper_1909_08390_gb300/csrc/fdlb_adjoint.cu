@@ -59,7 +59,7 @@ struct AdjParams {
 
 // ---- frozen-limiter interface: value coefficients over the window ----------
 
-// four-argument minmod choice as made by minmod4_bits: index 0..3 of the
+// four-argument minmod choice (the value dm_bits returns): index 0..3 of the
 // chosen argument, or -1 for zero
 __device__ __forceinline__ int minmod4_choice(long long a, long long b, long long c, long long d) {
   const bool same = ((a ^ b) >= 0) && ((a ^ c) >= 0) && ((a ^ d) >= 0);

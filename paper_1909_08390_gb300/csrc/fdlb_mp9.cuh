@@ -36,8 +36,25 @@
 
 namespace fdlb {
 
+// Bit casts.  On the device they are opaque register moves: a plain cast
+// lets the compiler fold integer tests of the bits (a zero magnitude, an
+// exponent range) back into binary64 compares, which run on the binary64
+// pipe -- about five per interface, a third of the march's binary64 work.
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ long long dbits(double x) {
+  long long r;
+  asm("mov.b64 %0, %1;" : "=l"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ double dfrom(long long b) {
+  double r;
+  asm("mov.b64 %0, %1;" : "=d"(r) : "l"(b));
+  return r;
+}
+#else
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ double dfrom(long long b) { return __longlong_as_double(b); }
+#endif
 constexpr long long kMag = 0x7fffffffffffffffLL;
 constexpr long long kSign = (long long)0x8000000000000000ULL;
 
@@ -46,18 +63,23 @@ __device__ __forceinline__ long long okey(long long b) { return b ^ ((b >> 63) &
 __device__ __forceinline__ long long kmin(long long a, long long b) { return a < b ? a : b; }
 __device__ __forceinline__ long long kmax(long long a, long long b) { return a < b ? b : a; }
 
-// four-argument minmod on bit patterns: if all four share a sign and none is
-// zero, the one of smallest magnitude, else +0.
-__device__ __forceinline__ long long minmod4_bits(long long a, long long b, long long c,
-                                                  long long d) {
-  const bool same = ((a ^ b) >= 0) && ((a ^ c) >= 0) && ((a ^ d) >= 0);
-  const long long ma = a & kMag, mb = b & kMag, mc = c & kMag, md = d & kMag;
-  const bool nz = (ma != 0) && (mb != 0) && (mc != 0) && (md != 0);
-  long long r = a, mr = ma;
-  if (mb < mr) { r = b; mr = mb; }
-  if (mc < mr) { r = c; mr = mc; }
-  if (md < mr) { r = d; }
-  return (same && nz) ? r : 0;
+// Bits of DM = minmod4(4 ca - cb, 4 cb - ca, ca, cb) (the curvature bound of
+// the MP limiter) with one binary64 operation.  DM is nonzero only if ca and
+// cb share a sign; then, with m the one of smaller magnitude (ca on a tie)
+// and M the other, 4 M - m has that sign and |4 M - m| >= 3 |M| >= |m|, so
+// DM is 4 m - M if that also has the sign and |4 m - M| <= |m|, else m, and
+// +0 when any of the four is zero or the signs differ.  On equal magnitudes
+// the earlier argument is taken, as a sequential minmod4 does.
+__device__ __forceinline__ long long dm_bits(double ca, double cb) {
+  const long long ba = dbits(ca), bb = dbits(cb);
+  const long long ma = ba & kMag, mb = bb & kMag;
+  const bool a_small = ma <= mb;
+  const double m = a_small ? ca : cb, M = a_small ? cb : ca;
+  const long long bm = a_small ? ba : bb, mm = a_small ? ma : mb;
+  const long long t = dbits(fma(4.0, m, -M));
+  const long long mt = t & kMag;
+  const bool nonzero = ((ba ^ bb) >= 0) && ((t ^ bm) >= 0) && (mm != 0) && (mt != 0);
+  return nonzero ? (mt <= mm ? t : bm) : 0;
 }
 
 // bits of x * 2^K, K = 1..3, as an ordering key.  Exact for normal x with
@@ -108,8 +130,7 @@ __device__ __forceinline__ double mp9_face_fp64(const Mp9Line& L, double& c1_out
   a = fma(B::b7, d[7], a);
   const double c1 = d[5] - d[4];  // C_{s+1}
   const double c0 = L.c0;
-  const long long dmp = minmod4_bits(dbits(fma(4.0, c0, -c1)), dbits(fma(4.0, c1, -c0)),
-                                     dbits(c0), dbits(c1));
+  const long long dmp = dm_bits(c0, c1);
   // bounds at twice their value: 2 d_0, 2 md = d_0 - DM+, 2 ul = 8 d_-1,
   // 2 lc = d_-1 + (8/3) DM-, and 2a
   const long long k_d0 = key_times_pow2<1>(dbits(d[4]));
@@ -142,8 +163,7 @@ __device__ __forceinline__ void mp9_march_fp64(const double* __restrict__ p, int
   for (int j = 0; j < 5; ++j) L.fs[j] = v[j + 4];
   L.cm1 = L.d[3] - L.d[2];
   L.c0 = L.d[4] - L.d[3];
-  L.dmm = minmod4_bits(dbits(fma(4.0, L.c0, -L.cm1)), dbits(fma(4.0, L.cm1, -L.c0)),
-                       dbits(L.c0), dbits(L.cm1));
+  L.dmm = dm_bits(L.cm1, L.c0);
 #pragma unroll
   for (int t = 0; t < NSTEP; ++t) {
     double c1;

@@ -35,3 +35,6 @@ extern "C" void mp9_line_march8(const double* ext, int n, int sgn, double* out) 
     fdlb::mp9_march_fp64<8>(ext + up, sgn, out + first, sgn);
   }
 }
+
+// bits of the device's one-operation DM = minmod4(4a - b, 4b - a, a, b)
+extern "C" long long mp9_dm_bits(double a, double b) { return fdlb::dm_bits(a, b); }

@@ -28,6 +28,8 @@ def mp9():
     lib.mp9_face.restype = ctypes.c_double
     lib.mp9_line.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
     lib.mp9_line_march8.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
+    lib.mp9_dm_bits.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib.mp9_dm_bits.restype = ctypes.c_longlong
     return lib
 
 
@@ -96,3 +98,43 @@ def test_line_march_matches_oracle_advection(oracle, mp9, sgn):
         want = oracle.advect_line(F, p, ds, bc=0)
         got = p * (a[1:] - a[:-1]) / ds
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+def _minmod4_literal(*xs):
+    """Sec. IV's four-argument minmod taken literally: the argument of
+    smallest magnitude (the first of equal ones) if all four are nonzero and
+    share a sign, else zero."""
+    if all(x > 0 for x in xs) or all(x < 0 for x in xs):
+        best = xs[0]
+        for x in xs[1:]:
+            if abs(x) < abs(best):
+                best = x
+        return best
+    return 0.0
+
+
+def _bits(x):
+    return int(np.array(x, dtype=np.float64).view(np.int64))
+
+
+def test_dm_one_operation_matches_four_argument_minmod(mp9):
+    """The march forms DM = minmod4(4a - b, 4b - a, a, b) from one fma
+    (the smaller-magnitude curvature m, the other M, and 4m - M): bitwise the
+    literal minmod4, +0 included, on random pairs and on ties, signed zeros,
+    equal magnitudes and the boundary 4|m| - |M| = |m|."""
+    rng = np.random.default_rng(5)
+    pairs = [(a, b) for a in (0.0, -0.0, 1.0, -1.0, 3.0, -3.0, 0.25, 4.0, 5e-324, -2.5e-300)
+             for b in (0.0, -0.0, 1.0, -1.0, 3.0, -3.0, 0.75, 4.0, 1e300, -7.0)]
+    pairs += [(x, 3.0 * x) for x in (1.0, -2.0, 0.1, 1e-200)]  # 4m - M = m
+    pairs += [(3.0 * x, x) for x in (1.0, -2.0, 0.1, 1e-200)]
+    pairs += [(x, x) for x in (1.0, -0.3)]
+    for _ in range(20000):
+        a, b = rng.normal(size=2) * rng.choice([1e-8, 1.0, 1e8], size=2)
+        if rng.random() < 0.3:
+            b = a * rng.choice([0.25, 0.26, 1.0, 2.9, 3.0, 3.1, 4.0, 5.0, -1.0])
+        pairs.append((float(a), float(b)))
+    for a, b in pairs:
+        # 4a is exact here, so 4a - b rounds once, as fma(4, a, -b) does
+        want = _minmod4_literal(4.0 * a - b, 4.0 * b - a, a, b)
+        got = mp9.mp9_dm_bits(a, b)
+        assert got == _bits(want if want != 0 else 0.0), (a, b, want)
