@@ -70,10 +70,10 @@ BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
 # profiles/stage_kernel_mixed_quadrant512.md, valid for the kernel sources
 # whose SHA-256 (over paper_1909_08390_gb300/csrc/*, sorted) is recorded here;
 # reported as null once the sources differ.
-TRAFFIC_SRC_SHA256 = "190d6fa93d055e9deef7d9b3294f9c054d43a36e394d715929679562c24f91ec"
+TRAFFIC_SRC_SHA256 = "2b8d92143b35c9f3951eb30ae0f763ead413f75630bb14945841487e0698095a"
 TRAFFIC_BYTES = {
-    "fp64": {"stage3": 3180514816, "stage4": 2332041984, "final": 1563790080},
-    "mixed": {"stage3": 528610560, "stage4": 666187520, "final": 418804480},
+    "fp64": {"stage3": 3182717696, "stage4": 2340981760, "final": 1574245632},
+    "mixed": {"stage3": 531635712, "stage4": 669009408, "final": 421227520},
 }
 
 
