@@ -34,7 +34,11 @@ namespace {
 
 constexpr int kTX = 16;   // cells per adjoint tile
 constexpr int kNT = 128;  // threads per adjoint CTA
-constexpr int kNI = kTX + 11;  // interfaces whose windows reach the tile: [x0-5, x0+TX+5]
+// Interfaces whose windows reach the tile's cells, per population: cell c
+// lies in the windows of interfaces c-3 .. c+5 (p >= 0) or c-4 .. c+4
+// (p < 0), so the tile needs [x0-3, x0+TX+4] or [x0-4, x0+TX+3].
+constexpr int kNI = kTX + 8;
+__device__ __forceinline__ int first_interface(int x0, int sgn) { return x0 - 4 + (sgn > 0 ? 1 : 0); }
 
 // Scalar accumulators of the adjoint (binary64, device):
 enum AdjScalar {
@@ -96,7 +100,7 @@ __device__ __forceinline__ void add_dm(double (&w)[9], int k, int ca, int cb, do
 // Recompute the forward interface value of the window v (same operations and
 // comparisons as mp9_face_fp64 inside the march) and return the coefficients
 // w of the chosen linear expression: Fhat = sum_m w[m] v[m].
-__device__ void mp9_linearize(const double (&v)[9], double (&w)[9]) {
+__device__ __forceinline__ void mp9_linearize(const double (&v)[9], double (&w)[9]) {
   using B = Mp9Coef;
   double d[8];
 #pragma unroll
@@ -116,29 +120,31 @@ __device__ void mp9_linearize(const double (&v)[9], double (&w)[9]) {
                                 dbits(c1));
   const int km = minmod4_choice(dbits(fma(4.0, cm1, -c0)), dbits(fma(4.0, c0, -cm1)), dbits(cm1),
                                 dbits(c0));
-  const double cand_p[4] = {fma(4.0, c0, -c1), fma(4.0, c1, -c0), c0, c1};
-  const double cand_m[4] = {fma(4.0, cm1, -c0), fma(4.0, c0, -cm1), cm1, c0};
-  const double dmp = kp < 0 ? 0.0 : cand_p[kp];
-  const double dmm = km < 0 ? 0.0 : cand_m[km];
+  // (selects, not indexed arrays, so that everything stays in registers)
+  auto pick4 = [](int k, double x0, double x1, double x2, double x3) {
+    return k == 0 ? x0 : k == 1 ? x1 : k == 2 ? x2 : k == 3 ? x3 : 0.0;
+  };
+  const double dmp = pick4(kp, fma(4.0, c0, -c1), fma(4.0, c1, -c0), c0, c1);
+  const double dmm = pick4(km, fma(4.0, cm1, -c0), fma(4.0, c0, -cm1), cm1, c0);
   // candidate keys (twice their value), as in the forward
   enum { Z = 0, D0 = 1, MD = 2, UL = 3, LC = 4, A = 5 };
-  long long k[5];
-  k[Z] = 0;
-  k[D0] = key_times_pow2<1>(dbits(d[4]));
-  k[MD] = okey(dbits(d[4] - dmp));
-  k[UL] = key_times_pow2<3>(dbits(d[3]));
-  k[LC] = okey(dbits(fma(8.0 / 3.0, dmm, d[3])));
+  const long long k_d0 = key_times_pow2<1>(dbits(d[4]));
+  const long long k_md = okey(dbits(d[4] - dmp));
+  const long long k_ul = key_times_pow2<3>(dbits(d[3]));
+  const long long k_lc = okey(dbits(fma(8.0 / 3.0, dmm, d[3])));
   const long long ka = key_times_pow2<1>(dbits(a));
+  auto key = [&](int i) {
+    return i == D0 ? k_d0 : i == MD ? k_md : i == UL ? k_ul : i == LC ? k_lc : i == A ? ka : 0LL;
+  };
   // lo = kmax(kmin(0, kmin(k_d0, k_md)), kmin(0, kmin(k_ul, k_lc))), with the
   // forward's tie rules: kmin(a, b) = a < b ? a : b, kmax(a, b) = a < b ? b : a
-  auto kmin_i = [&](int i, int j) { return k[i] < k[j] ? i : j; };
-  auto kmax_i = [&](int i, int j) { return k[i] < k[j] ? j : i; };
+  auto kmin_i = [&](int i, int j) { return key(i) < key(j) ? i : j; };
+  auto kmax_i = [&](int i, int j) { return key(i) < key(j) ? j : i; };
   const int lo = kmax_i(kmin_i(Z, kmin_i(D0, MD)), kmin_i(Z, kmin_i(UL, LC)));
   const int hi = kmin_i(kmax_i(Z, kmax_i(D0, MD)), kmax_i(Z, kmax_i(UL, LC)));
   // r = kmin(kmax(ka, lo), hi)
-  int sel = (ka < k[lo]) ? lo : A;
-  const long long ks = sel == A ? ka : k[sel];
-  if (!(ks < k[hi])) sel = hi;
+  int sel = (ka < key(lo)) ? lo : A;
+  if (!(key(sel) < key(hi))) sel = hi;
 #pragma unroll
   for (int m = 0; m < 9; ++m) w[m] = 0.0;
   w[4] = 1.0;  // F_s
@@ -217,13 +223,32 @@ struct EqAdj {
 
 // ---- the three adjoint stage kernels -------------------------------------
 
-// Shared memory: per population, the contributions of the tile's interfaces
-// to their 9 window cells.
-template <int P>
+// Shared memory: per population, the frozen-limiter weights of the tile's
+// interfaces over their 9 window cells and the adjoint each interface
+// receives; the gathered adjoint of the advected array; and the Hermite
+// coefficient tables of the equilibrium derivatives, c_lk l and
+// c_lk l(l-1)/2 (c_lk = w_k He_l(p_k)/l!), formed once per CTA.
+template <int QP, int QC>
 struct AdjSmem {
-  double ctr[P][kNI][9];
+  static constexpr int P = QP + QC;
+  double wts[P][kNI][9];
+  double ifb[P][kNI];
   double fbar[P][kTX];
+  double cup[QP * QP], cTp[QP * QP], cuc[QC * QC], cTc[QC * QC];
 };
+
+template <int QP, int QC>
+__device__ __forceinline__ void fill_deriv_tables(const DevParams& p, AdjSmem<QP, QC>& sm) {
+  for (int t = threadIdx.x; t < QP * QP + QC * QC; t += kNT) {
+    const bool phi = t < QP * QP;
+    const int Q = phi ? QP : QC;
+    const int lk = phi ? t : t - QP * QP;
+    const int l = lk / Q, k = lk % Q;
+    const double c = (phi ? p.wHp : p.wHc)[l * kMaxQ + k];
+    (phi ? sm.cup : sm.cuc)[lk] = c * (double)l;
+    (phi ? sm.cTp : sm.cTc)[lk] = c * (0.5 * l * (l - 1));
+  }
+}
 
 __device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
 
@@ -233,10 +258,11 @@ __device__ __forceinline__ int slot_cell(int i, int m, int sgn) {
 }
 
 // dt L^T: the adjoint of X = dt L(Fin) for the tile's cells, every population,
-// into sm.fbar.  Xbar(pop, cell) gives the adjoint of X at any cell.
+// into sm.fbar (each interface's adjoint times its window weights, summed).
+// Xbar(pop, cell) gives the adjoint of X at any cell.
 template <int QP, int QC, typename XbarFn>
 __device__ __forceinline__ void advect_adjoint(const DevParams& p, const double* Fin, int x0,
-                                               AdjSmem<(QP + QC)>& sm, XbarFn Xbar) {
+                                               AdjSmem<QP, QC>& sm, XbarFn Xbar) {
   constexpr int P = QP + QC;
   const int nx = p.nx;
   const int64_t N = p.N;
@@ -244,15 +270,16 @@ __device__ __forceinline__ void advect_adjoint(const DevParams& p, const double*
   for (int t = tid; t < P * kNI; t += kNT) {
     const int pop = t / kNI;
     const int ii = t % kNI;
-    const int i = x0 - 5 + ii;  // interface index
-    double* c = sm.ctr[pop][ii];
+    const double px = p.px[pop];
+    const int sgn = px >= 0.0 ? 1 : -1;
+    const int i = first_interface(x0, sgn) + ii;  // interface index
+    double* c = sm.wts[pop][ii];
     if (i < 0 || i > nx) {
 #pragma unroll
       for (int m = 0; m < 9; ++m) c[m] = 0.0;
+      sm.ifb[pop][ii] = 0.0;
       continue;
     }
-    const double px = p.px[pop];
-    const int sgn = px >= 0.0 ? 1 : -1;
     double v[9];
 #pragma unroll
     for (int m = 0; m < 9; ++m) v[m] = Fin[pop * N + clampi(slot_cell(i, m, sgn), nx)];
@@ -262,9 +289,9 @@ __device__ __forceinline__ void advect_adjoint(const DevParams& p, const double*
     const double cp = p.dtdx * px;
     const double xl = (i - 1 >= 0) ? Xbar(pop, i - 1) : 0.0;
     const double xr = (i <= nx - 1) ? Xbar(pop, i) : 0.0;
-    const double fb = cp * (xl - xr);
+    sm.ifb[pop][ii] = cp * (xl - xr);
 #pragma unroll
-    for (int m = 0; m < 9; ++m) c[m] = fb * w[m];
+    for (int m = 0; m < 9; ++m) c[m] = w[m];
   }
   __syncthreads();
   // gather: cell c sits at slot m = c - i + 5 of interface i (p >= 0, i in
@@ -278,11 +305,15 @@ __device__ __forceinline__ void advect_adjoint(const DevParams& p, const double*
     if (cell < nx) {
       const int sgn = p.px[pop] >= 0.0 ? 1 : -1;
       const int ifirst = sgn > 0 ? cell - 3 : cell - 4;
+      const int ibase = first_interface(x0, sgn);
 #pragma unroll
       for (int t9 = 0; t9 < 9; ++t9) {
         const int i = ifirst + t9;
         const int m = sgn > 0 ? cell - i + 5 : i + 4 - cell;
-        if (i >= 0 && i <= nx) acc += sm.ctr[pop][i - (x0 - 5)][m];
+        if (i >= 0 && i <= nx) {
+          const int ii = i - ibase;
+          acc = fma(sm.ifb[pop][ii], sm.wts[pop][ii][m], acc);
+        }
       }
       if (cell == 0 || cell == nx - 1) {
         // slots whose window cell lies outside [0, nx) and is clamped to `cell`
@@ -292,7 +323,7 @@ __device__ __forceinline__ void advect_adjoint(const DevParams& p, const double*
           for (int m = 0; m < 9; ++m) {
             const int sc = slot_cell(i, m, sgn);
             if ((cell == 0 && sc < 0) || (cell == nx - 1 && sc > nx - 1))
-              acc += sm.ctr[pop][i - (x0 - 5)][m];
+              acc = fma(sm.ifb[pop][i - ibase], sm.wts[pop][i - ibase][m], acc);
           }
         }
       }
@@ -325,10 +356,12 @@ __device__ __forceinline__ double cell_sum(double v) {
   return v;
 }
 
-// One node's equilibrium factor and its u- and T-derivatives (Eq. gExpanded).
+// One node's equilibrium factor and its u- and T-derivatives (Eq. gExpanded),
+// with the derivative coefficients c_lk l and c_lk l(l-1)/2 from the tables.
 template <int Q>
-__device__ __forceinline__ void node_derivs(const double* wH, int k, double u, double T, double& g,
-                                            double& gu, double& gT) {
+__device__ __forceinline__ void node_derivs(const double* wH, const double* cu, const double* cT,
+                                            int k, double u, double T, double& g, double& gu,
+                                            double& gT) {
   double a[Q];
   a[0] = 1.0;
   if (Q > 1) a[1] = u;
@@ -340,10 +373,9 @@ __device__ __forceinline__ void node_derivs(const double* wH, int k, double u, d
   gT = 0.0;
 #pragma unroll
   for (int l = 0; l < Q; ++l) {
-    const double c = wH[l * kMaxQ + k];
-    g = fma(c, a[l], g);
-    if (l >= 1) gu = fma(c * (double)l, a[l - 1], gu);
-    if (l >= 2) gT = fma(c * (0.5 * l * (l - 1)), a[l - 2], gT);
+    g = fma(wH[l * kMaxQ + k], a[l], g);
+    if (l >= 1) gu = fma(cu[l * Q + k], a[l - 1], gu);
+    if (l >= 2) gT = fma(cT[l * Q + k], a[l - 2], gT);
   }
 }
 
@@ -354,27 +386,41 @@ struct PopEq {
   double dk;          // its derivative with respect to D + K at fixed n, u, T
 };
 
+__device__ __forceinline__ PopEq phi_eq(double n, double g, double gu, double gT) {
+  return PopEq{n * g, g, n * gu, n * gT, 0.0};
+}
+__device__ __forceinline__ PopEq chi_eq(double kc, double n, double T, double g, double gu,
+                                        double gT) {
+  // chi^eq = (D+K-d) T n h
+  return PopEq{kc * T * n * g, kc * T * g, kc * T * n * gu, kc * n * (g + T * gT), T * n * g};
+}
+
+// The equilibria of the sub-thread's populations sub and sub + kSub.  On the
+// (8, 8) lattice they are the phi and chi populations of one node, whose
+// factors are evaluated once.
 template <int QP, int QC>
-__device__ __forceinline__ PopEq pop_eq(const DevParams& p, int pop, double n, double u, double T) {
-  PopEq r;
+__device__ __forceinline__ void pop_eqs(const DevParams& p, const AdjSmem<QP, QC>& sm, int sub,
+                                        double n, double u, double T, PopEq (&q)[2]) {
+  constexpr int P = QP + QC;
   double g, gu, gT;
-  if (pop < QP) {
-    node_derivs<QP>(p.wHp, pop, u, T, g, gu, gT);
-    r.fe = n * g;
-    r.dn = g;
-    r.du = n * gu;
-    r.dT = n * gT;
-    r.dk = 0.0;
+  if constexpr (QP == QC && QP == kSub) {
+    node_derivs<QP>(p.wHp, sm.cup, sm.cTp, sub, u, T, g, gu, gT);
+    q[0] = phi_eq(n, g, gu, gT);
+    q[1] = chi_eq(p.kchi, n, T, g, gu, gT);
   } else {
-    node_derivs<QC>(p.wHc, pop - QP, u, T, g, gu, gT);
-    const double kc = p.kchi;
-    r.fe = kc * T * n * g;
-    r.dn = kc * T * g;
-    r.du = kc * T * n * gu;
-    r.dT = kc * n * (g + T * gT);
-    r.dk = T * n * g;  // chi^eq = (D+K-d) T n h
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int pop = sub + kSub * r;
+      if (pop >= P) break;
+      if (pop < QP) {
+        node_derivs<QP>(p.wHp, sm.cup, sm.cTp, pop, u, T, g, gu, gT);
+        q[r] = phi_eq(n, g, gu, gT);
+      } else {
+        node_derivs<QC>(p.wHc, sm.cuc, sm.cTc, pop - QP, u, T, g, gu, gT);
+        q[r] = chi_eq(p.kchi, n, T, g, gu, gT);
+      }
+    }
   }
-  return r;
 }
 
 // The cell's (n, j, e) from the sub-thread's populations v[0..1].
@@ -421,9 +467,10 @@ template <int QP, int QC>
 __global__ void __launch_bounds__(kNT) adj4_kernel(const __grid_constant__ DevParams p,
                                                    const __grid_constant__ AdjParams a) {
   constexpr int P = QP + QC;
-  __shared__ AdjSmem<P> sm;
+  __shared__ AdjSmem<QP, QC> sm;
   const StageCoef& sc = p.sc;
   const int x0 = blockIdx.x * kTX;
+  fill_deriv_tables<QP, QC>(p, sm);  // read after advect_adjoint's barriers
   const int64_t N = p.N;
   // X4bar = -wt4 Gbar
   advect_adjoint<QP, QC>(p, a.F4s, x0, sm,
@@ -445,13 +492,12 @@ __global__ void __launch_bounds__(kNT) adj4_kernel(const __grid_constant__ DevPa
   const double inv = 1.0 / (1.0 - sc.a44e4);
   double R4b[2] = {0.0, 0.0}, G[2] = {0.0, 0.0};
   PopEq q[2];
+  pop_eqs<QP, QC>(p, sm, sub, n, u, T, q);
   double nb = 0.0, ub = 0.0, Tb = 0.0, kb = 0.0;
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int pop = sub + kSub * r;
-    if (pop >= P) break;
-    q[r] = pop_eq<QP, QC>(p, pop, n, u, T);
-    if (!live) continue;
+    if (pop >= P || !live) break;
     G[r] = a.Gbar[pop * N + cell];
     const double f4b = sm.fbar[pop][lc];
     const double D4 = (F4[r] - q[r].fe) * inv;  // R4 - E4
@@ -485,9 +531,10 @@ template <int QP, int QC>
 __global__ void __launch_bounds__(kNT) adj3_kernel(const __grid_constant__ DevParams p,
                                                    const __grid_constant__ AdjParams a) {
   constexpr int P = QP + QC;
-  __shared__ AdjSmem<P> sm;
+  __shared__ AdjSmem<QP, QC> sm;
   const StageCoef& sc = p.sc;
   const int x0 = blockIdx.x * kTX;
+  fill_deriv_tables<QP, QC>(p, sm);  // read after advect_adjoint's barriers
   const int64_t N = p.N;
   advect_adjoint<QP, QC>(p, a.F3s, x0, sm, [&](int pop, int c) { return a.X3bar[pop * N + c]; });
   const int lc = threadIdx.x / kSub, sub = threadIdx.x % kSub;
@@ -513,12 +560,13 @@ __global__ void __launch_bounds__(kNT) adj3_kernel(const __grid_constant__ DevPa
   const double inv = 1.0 / (1.0 - sc.a33e3);
   double R3b[2] = {0.0, 0.0}, A4b[2] = {0.0, 0.0}, G[2] = {0.0, 0.0};
   double nb = 0.0, ub = 0.0, Tb = 0.0, kb = 0.0;
+  PopEq qs[2];
+  pop_eqs<QP, QC>(p, sm, sub, n, u, T, qs);
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int pop = sub + kSub * r;
-    if (pop >= P) break;
-    const PopEq q = pop_eq<QP, QC>(p, pop, n, u, T);
-    if (!live) continue;
+    if (pop >= P || !live) break;
+    const PopEq& q = qs[r];
     A4b[r] = a.A4bar[pop * N + cell];
     G[r] = a.Gbar[pop * N + cell];
     const double f3b = sm.fbar[pop][lc];
@@ -537,12 +585,13 @@ __global__ void __launch_bounds__(kNT) adj3_kernel(const __grid_constant__ DevPa
                                    cell_sum(kb));
   if (sub == 0 && live) s[6] = ea.dk;
   // explicit part R3 = F - k3 D - at32 X2, A4 and A_fin: adjoints of F, D, X2
+  PopEq q0[2];
+  pop_eqs<QP, QC>(p, sm, sub, n0, u0, T0, q0);
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int pop = sub + kSub * r;
-    if (pop >= P) break;
-    const double e0p = pop_eq<QP, QC>(p, pop, n0, u0, T0).fe;
-    if (!live) continue;
+    if (pop >= P || !live) break;
+    const double e0p = q0[r].fe;
     const double rb = R3b[r] + (pop < QP ? fma(p.p2[pop], ea.re, fma(p.px[pop], ea.rj, ea.rn)) : ea.re);
     const double D = Fn[r] - e0p;
     s[3] -= rb * D;
@@ -566,9 +615,10 @@ template <int QP, int QC>
 __global__ void __launch_bounds__(kNT) adj2_kernel(const __grid_constant__ DevParams p,
                                                    const __grid_constant__ AdjParams a) {
   constexpr int P = QP + QC;
-  __shared__ AdjSmem<P> sm;
+  __shared__ AdjSmem<QP, QC> sm;
   const StageCoef& sc = p.sc;
   const int x0 = blockIdx.x * kTX;
+  fill_deriv_tables<QP, QC>(p, sm);  // read after advect_adjoint's barriers
   const int64_t N = p.N;
   advect_adjoint<QP, QC>(p, a.F2s, x0, sm, [&](int pop, int c) { return a.X2bar[pop * N + c]; });
   const int lc = threadIdx.x / kSub, sub = threadIdx.x % kSub;
@@ -587,12 +637,13 @@ __global__ void __launch_bounds__(kNT) adj2_kernel(const __grid_constant__ DevPa
   const double inv_n0 = 1.0 / n0, u0 = j0 * inv_n0, T0 = (e0 - n0 * u0 * u0) * inv_n0 * p.invDK;
   double Dt[2] = {0.0, 0.0};
   double nb = 0.0, ub = 0.0, Tb = 0.0, kb = 0.0;
+  PopEq qs[2];
+  pop_eqs<QP, QC>(p, sm, sub, n0, u0, T0, qs);
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int pop = sub + kSub * r;
-    if (pop >= P) break;
-    const PopEq q = pop_eq<QP, QC>(p, pop, n0, u0, T0);
-    if (!live) continue;
+    if (pop >= P || !live) break;
+    const PopEq& q = qs[r];
     const double f2b = sm.fbar[pop][lc];
     Dt[r] = a.Dbar[pop * N + cell] + sc.c2 * f2b;  // total adjoint of D
     const double eb = f2b - Dt[r];                  // F2 = E0 + c2 D, D = F - E0
