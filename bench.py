@@ -68,21 +68,25 @@ BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # the ncu captures summarised in profiles/stage_kernel_fp64_quadrant512.md and
 # profiles/stage_kernel_mixed_quadrant512.md, valid for the kernel sources
-# whose SHA-256 (over paper_1909_08390_gb300/csrc/*, sorted) is recorded here;
-# reported as null once the sources differ.
-TRAFFIC_SRC_SHA256 = "2b8d92143b35c9f3951eb30ae0f763ead413f75630bb14945841487e0698095a"
+# whose SHA-256 (over STAGE_KERNEL_SOURCES, in that order) is recorded here;
+# reported as null once those sources differ.
+TRAFFIC_SRC_SHA256 = "f0b7ddef3e09d13a898de9ac5a8bfcc76d21f472daba6fcefb6ad2d78c62faf7"
 TRAFFIC_BYTES = {
     "fp64": {"stage3": 3182717696, "stage4": 2340981760, "final": 1574245632},
     "mixed": {"stage3": 531635712, "stage4": 669009408, "final": 421227520},
 }
 
 
+# The sources the stage kernels are compiled from.
+STAGE_KERNEL_SOURCES = ("fdlb_device.cuh", "fdlb_internal.h", "fdlb_kernels.cu", "fdlb_mixed.cu",
+                        "fdlb_mp9.cuh")
+
+
 def _kernel_sources_sha256():
-    import glob
     import hashlib
     h = hashlib.sha256()
-    for path in sorted(glob.glob(os.path.join(ROOT, "paper_1909_08390_gb300", "csrc", "*"))):
-        with open(path, "rb") as f:
+    for name in STAGE_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1909_08390_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
