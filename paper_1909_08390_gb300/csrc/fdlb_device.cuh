@@ -243,6 +243,49 @@ __device__ __forceinline__ void accumulate(const DevParams& p, MomentsF& m, int 
   }
 }
 
+// The same sums for two cells at once, in packed binary32 pairs (sm_100 and
+// later: one instruction per two lanes).  Each lane performs exactly the
+// operations of the scalar version, so the sums are bitwise the same.
+struct MomentsF2 {
+  float2 nh, nl, jxh, jxl, jyh, jyl, eh, el;
+};
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, f2s(-1.0f), a);  // a - b, rounded once
+}
+__device__ __forceinline__ void two_sum_acc2(float2& hi, float2& lo, float2 x) {
+  const float2 s = __fadd2_rn(hi, x);
+  const float2 bb = sub2(s, hi);
+  const float2 err = __fadd2_rn(sub2(hi, sub2(s, bb)), sub2(x, bb));
+  hi = s;
+  lo = __fadd2_rn(lo, err);
+}
+__device__ __forceinline__ void two_prod_acc2(float2& hi, float2& lo, float ph, float pl,
+                                              float2 v) {
+  const float2 prod = __fmul2_rn(f2s(ph), v);
+  const float2 nprod = __fmul2_rn(f2s(-ph), v);   // -prod exactly
+  const float2 perr = __ffma2_rn(f2s(ph), v, nprod);  // exact: ph * v - prod
+  two_sum_acc2(hi, lo, prod);
+  lo = __fadd2_rn(lo, __ffma2_rn(f2s(pl), v, perr));
+}
+template <int DIM, int QP, int QC>
+__device__ __forceinline__ void accumulate2(const DevParams& p, MomentsF2& m, int pop, float2 v) {
+  using L = Lat<DIM, QP, QC>;
+  if (pop < L::NPHI) {
+    two_sum_acc2(m.nh, m.nl, v);
+    two_prod_acc2(m.jxh, m.jxl, p.pxh[pop], p.pxl[pop], v);
+    if (DIM == 2) two_prod_acc2(m.jyh, m.jyl, p.pyh[pop], p.pyl[pop], v);
+    two_prod_acc2(m.eh, m.el, p.p2h[pop], p.p2l[pop], v);
+  } else {
+    two_sum_acc2(m.eh, m.el, v);
+  }
+}
+// lane i (0 or 1) of a pair of sums
+__device__ __forceinline__ MomentsF lane(const MomentsF2& m, int i) {
+  auto g = [i](float2 x) { return i == 0 ? x.x : x.y; };
+  return MomentsF{g(m.nh), g(m.nl), g(m.jxh), g(m.jxl), g(m.jyh), g(m.jyl), g(m.eh), g(m.el)};
+}
+
 __device__ __forceinline__ Moments to_fp64(const Moments& m) { return m; }
 __device__ __forceinline__ Moments to_fp64(const MomentsF& m) {
   return Moments{(double)m.nh + (double)m.nl, (double)m.jxh + (double)m.jxl,

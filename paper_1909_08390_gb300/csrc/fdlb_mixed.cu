@@ -296,6 +296,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   MomentsF mom[CPT];
 #pragma unroll
   for (int k = 0; k < CPT; ++k) mom[k] = {};
+  MomentsF2 mom2 = {};  // the two cells' sums when CPT == 2
   const CoefS<float> sc(p.sc);
   const float arelax = STAGE == kStage3 ? sc.c2 : (STAGE == kStage4 ? sc.a33e3 : sc.a44e4);
   const float dtdx = (float)geo.dtdx, dtdy = (float)geo.dtdy;
@@ -308,6 +309,25 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   // each thread copies, and later reads, only its own staged cells, so its
   // own wait on the copies orders them
   using GR = GroupRec<DIM, QP, QC, G>;
+  // Group order.  2-D groups with a record plan run x-block-major: the 8
+  // groups that share the x factors A of one block of G columns come one
+  // after another (rows ky = 0..QP-1), phi before chi, so that only B (and C
+  // once) change from one group to the next.  Otherwise groups run in
+  // population order.
+  constexpr int NG = (L::P + G - 1) / G;
+  auto gpop = [](int gi) -> int {
+    if constexpr (DIM == 2 && GR::kOn) {
+      constexpr int per_half = L::NPHI / G;
+      const int half = gi / per_half, r = gi % per_half;
+      return half * L::NPHI + (r % QP) * QP + (r / QP) * G;
+    } else {
+      return gi * G;
+    }
+  };
+  // record component held by each slot of sm.rbuf (the same in every thread)
+  int rcomp[GR::kOn ? GR::NS : 1];
+#pragma unroll
+  for (int sl = 0; sl < (GR::kOn ? GR::NS : 1); ++sl) rcomp[sl] = -1;
   auto prefetch = [&](int gfirst) {
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -322,7 +342,8 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
 #pragma unroll
       for (int sl = 0; sl < GR::NS; ++sl) {
         const int comp = GR::comp(gfirst, sl);
-        if (comp < 0) continue;
+        if (comp < 0 || comp == rcomp[sl]) continue;  // absent, or still there
+        rcomp[sl] = comp;
         const float* __restrict__ src = rbase + (int64_t)comp * N;
 #pragma unroll
         for (int j = 0; j < J; ++j)
@@ -331,8 +352,9 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
     }
     cp_async_commit();
   };
-  prefetch(0);
-  for (int g0 = 0; g0 < L::P; g0 += G) {
+  prefetch(gpop(0));
+  for (int gi = 0; gi < NG; ++gi) {
+    const int g0 = gpop(gi);  // first population of the group
     // the running explicit parts of the own cells (stage 4, final), early
     float a4v[CPT][G], afv[CPT][G];
     if constexpr (STAGE != kStage3) {
@@ -380,7 +402,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
       }
     }
     __syncthreads();
-    if (g0 + G < L::P) prefetch(g0 + G);  // overlaps the march and pass 1
+    if (gi + 1 < NG) prefetch(gpop(gi + 1));  // overlaps the march and pass 1
     // ---- every interface value once, marching upwind -> downwind
     {
       const int pop = g0 + tg;
@@ -399,6 +421,48 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
     }
     __syncthreads();
     // ---- flux difference and explicit part of the own cells
+    if constexpr (CPT == 2) {
+      // the thread's two cells in lockstep, as packed binary32 pairs (lane 1
+      // of a cell outside the grid computes on unused values, never stored)
+      const int o0 = lys[0] * TX + lxs[0], o1 = lys[1] * TX + lxs[1];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int pop = g0 + g;
+        if (pop >= L::P) break;
+        const float2 dfx = sub2(make_float2(sm.hx[g][lys[0]][lxs[0] + 1], sm.hx[g][lys[1]][lxs[1] + 1]),
+                                make_float2(sm.hx[g][lys[0]][lxs[0]], sm.hx[g][lys[1]][lxs[1]]));
+        float2 X = __fmul2_rn(f2s(dtdx * p.pxh[pop]), dfx);
+        if constexpr (DIM == 2) {
+          const float2 dfy = sub2(make_float2(sm.hy[g][lxs[0]][lys[0] + 1], sm.hy[g][lxs[1]][lys[1] + 1]),
+                                  make_float2(sm.hy[g][lxs[0]][lys[0]], sm.hy[g][lxs[1]][lys[1]]));
+          X = __ffma2_rn(f2s(dtdy * p.pyh[pop]), dfy, X);
+        }
+        const int64_t e0 = (int64_t)pop * N + cell[0], e1 = (int64_t)pop * N + cell[1];
+        const float2 d = make_float2(sm.ownd[g][o0], sm.ownd[g][o1]);
+        float2 R;
+        if constexpr (STAGE == kStage3) {
+          const float2 f = make_float2(sm.ownv[g][o0], sm.ownv[g][o1]);
+          R = __ffma2_rn(f2s(-sc.at32), X, __ffma2_rn(f2s(-sc.k3), d, f));
+          const float2 a4 = __ffma2_rn(f2s(-sc.at42), X, __ffma2_rn(f2s(-sc.k4), d, f));
+          const float2 af = __ffma2_rn(f2s(-sc.wt2), X, __ffma2_rn(f2s(-sc.kf), d, f));
+          if (valid[0]) { R3[e0] = R.x; A4[e0] = a4.x; Af[e0] = af.x; }
+          if (valid[1]) { R3[e1] = R.y; A4[e1] = a4.y; Af[e1] = af.y; }
+        } else if constexpr (STAGE == kStage4) {
+          R = __ffma2_rn(f2s(-sc.at43), X,
+                         __ffma2_rn(f2s(-sc.a43e3), d, make_float2(a4v[0][g], a4v[1][g])));
+          const float2 af = __ffma2_rn(f2s(-sc.wt3), X,
+                                       __ffma2_rn(f2s(-sc.w3e3), d, make_float2(afv[0][g], afv[1][g])));
+          if (valid[0]) { A4[e0] = R.x; Af[e0] = af.x; }
+          if (valid[1]) { A4[e1] = R.y; Af[e1] = af.y; }
+        } else {
+          R = __ffma2_rn(f2s(-sc.wt4), X,
+                         __ffma2_rn(f2s(-sc.w4e4), d, make_float2(afv[0][g], afv[1][g])));
+          if (valid[0]) F[e0] = R.x;
+          if (valid[1]) F[e1] = R.y;
+        }
+        accumulate2<DIM, QP, QC>(p, mom2, pop, R);
+      }
+    } else {
 #pragma unroll
     for (int k = 0; k < CPT; ++k) {
       if (!valid[k]) continue;
@@ -430,7 +494,12 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
         accumulate<DIM, QP, QC>(p, mom[k], pop, R);
       }
     }
+    }
     __syncthreads();
+  }
+  if constexpr (CPT == 2) {
+    mom[0] = lane(mom2, 0);
+    mom[1] = lane(mom2, 1);
   }
   // ---- records of the stage's explicit parts (the next kernel relaxes them)
 #pragma unroll

@@ -196,9 +196,29 @@ struct Mp9LineF {
   float cm1, c0, dmm;
 };
 
+// Three-input minimum and maximum (one instruction on sm_100 and later).
+__device__ __forceinline__ float fmin3f(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+#else
+  return fminf(fminf(a, b), c);
+#endif
+}
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+#else
+  return fmaxf(fmaxf(a, b), c);
+#endif
+}
+
 __device__ __forceinline__ float minmod4f(float a, float b, float c, float d) {
-  const float lo = fminf(fminf(a, b), fminf(c, d));
-  const float hi = fmaxf(fmaxf(a, b), fmaxf(c, d));
+  const float lo = fmin3f(a, b, fminf(c, d));
+  const float hi = fmax3f(a, b, fmaxf(c, d));
   return lo > 0.0f ? lo : (hi < 0.0f ? hi : 0.0f);
 }
 
@@ -218,8 +238,8 @@ __device__ __forceinline__ float mp9_face_fp32(const Mp9LineF& L, float& c1_out,
   const float md = 0.5f * (d[4] - dmp);
   const float ul = 4.0f * d[3];
   const float lc = fmaf(4.0f / 3.0f, L.dmm, 0.5f * d[3]);
-  const float lo = fmaxf(fminf(0.0f, fminf(d[4], md)), fminf(0.0f, fminf(ul, lc)));
-  const float hi = fminf(fmaxf(0.0f, fmaxf(d[4], md)), fmaxf(0.0f, fmaxf(ul, lc)));
+  const float lo = fmaxf(fmin3f(0.0f, d[4], md), fmin3f(0.0f, ul, lc));
+  const float hi = fminf(fmax3f(0.0f, d[4], md), fmax3f(0.0f, ul, lc));
   c1_out = c1;
   dmp_out = dmp;
   return L.fs[0] + fminf(fmaxf(a, lo), hi);
