@@ -92,6 +92,31 @@ __device__ __forceinline__ DF df_of(double x) {
 }
 __device__ __forceinline__ float df_round(DF x) { return __fadd_rn(x.hi, x.lo); }
 
+// The same pair arithmetic on two lanes at once (packed binary32, sm_100
+// and later); each lane performs exactly the operations of DF.
+struct DF2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 neg2(float2 x) { return __fmul2_rn(x, f2s(-1.0f)); }
+__device__ __forceinline__ DF2 df_quick2(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  return {s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ DF2 df_add2(DF2 x, DF2 y) {
+  const float2 s = __fadd2_rn(x.hi, y.hi);
+  const float2 bb = sub2(s, x.hi);
+  const float2 e = __fadd2_rn(sub2(x.hi, sub2(s, bb)), sub2(y.hi, bb));
+  return df_quick2(s, __fadd2_rn(e, __fadd2_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ DF2 df_mul2(DF2 x, DF2 y) {
+  const float2 pr = __fmul2_rn(x.hi, y.hi);
+  float2 e = __ffma2_rn(x.hi, y.hi, neg2(pr));
+  e = __ffma2_rn(x.hi, y.lo, e);
+  e = __ffma2_rn(x.lo, y.hi, e);
+  return df_quick2(pr, e);
+}
+__device__ __forceinline__ DF2 df_bcast(DF x) { return {f2s(x.hi), f2s(x.lo)}; }
+
 // One axis of the equilibrium factors (Eq. gExpanded) times `scale`, in pair
 // arithmetic: the recurrence a_0 = s, a_1 = s u, a_l = u a_{l-1} +
 // (l-1)(T-1) a_{l-2}, then g_k = sum_l [w_k He_l(p_k)/l!] a_l, summed as even
@@ -106,8 +131,31 @@ __device__ __forceinline__ void axis_g_df(const float* ch, const float* cl, DF u
 #pragma unroll
   for (int l = 2; l < Q; ++l)
     a[l] = df_add(df_mul(u, a[l - 1]), df_mul(df_mul(DF{(float)(l - 1), 0.0f}, tm1), a[l - 2]));
+  // nodes k and k+1 in the two lanes of packed pairs, then an odd one out
+  constexpr int NH = (Q + 1) / 2;
 #pragma unroll
-  for (int k = 0; k < (Q + 1) / 2; ++k) {
+  for (int k = 0; k + 1 < NH; k += 2) {
+    auto coef = [&](int l) {
+      return DF2{make_float2(ch[l * kMaxQ + k], ch[l * kMaxQ + k + 1]),
+                 make_float2(cl[l * kMaxQ + k], cl[l * kMaxQ + k + 1])};
+    };
+    DF2 e = df_mul2(coef(0), df_bcast(a[0]));
+    DF2 o = DF2{f2s(0.0f), f2s(0.0f)};
+#pragma unroll
+    for (int l = 1; l < Q; ++l) {
+      const DF2 t = df_mul2(coef(l), df_bcast(a[l]));
+      if (l & 1) o = df_add2(o, t);
+      else e = df_add2(e, t);
+    }
+    const DF2 sum = df_add2(e, o);
+    const DF2 dif = df_add2(e, DF2{neg2(o.hi), neg2(o.lo)});
+    g[k] = DF{sum.hi.x, sum.lo.x};
+    if (Q - 1 - k != k) g[Q - 1 - k] = DF{dif.hi.x, dif.lo.x};
+    g[k + 1] = DF{sum.hi.y, sum.lo.y};
+    if (Q - 2 - k != k + 1) g[Q - 2 - k] = DF{dif.hi.y, dif.lo.y};
+  }
+  if constexpr (NH % 2 == 1) {
+    constexpr int k = NH - 1;
     DF e = df_mul(DF{ch[k], cl[k]}, a[0]);
     DF o = DF{0.0f, 0.0f};
 #pragma unroll
@@ -371,33 +419,65 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
     }
     // ---- stage the group: relaxed advected values on tile + halo
     cp_async_wait_all();
+    // The equilibrium is A B (phi) or C (A B) (chi) from the record slots,
+    // D = R - F_eq, and stage 3 stages F2 = E0 + c2 D, stages 4 and final
+    // F = R - a_ii e_i D; every operation is rounded on its own, so the
+    // paired (packed) and single forms below agree bit for bit.
+    auto keep = [&](int g, int j, float w, float d, float v) {
+      (&sm.tile[g][0][0])[soff[j]] = w;
+      if (oidx[j] >= 0) {
+        sm.ownd[g][oidx[j]] = d;
+        if (STAGE == kStage3) sm.ownv[g][oidx[j]] = v;
+      }
+    };
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int pop = g0 + g;
       if (pop >= L::P) break;
+      if constexpr (GR::kOn) {
+        const int nphi = DIM == 2 ? QP * QP : QP;
+        const bool chi = pop >= nphi;
+        const int k = chi ? pop - nphi : pop;
+        const int ia = (DIM == 2 ? k % QP : k) - GR::a0(g0);
+        // pairs of staged cells; a halo corner or a slot past the staged
+        // cells computes on values that are not kept (the last slot's index
+        // is clamped into the arrays)
 #pragma unroll
-      for (int j = 0; j < J; ++j) {
-        if (goff[j] < 0) continue;
-        const int e = tid + j * NT;
-        const float v = sm.raw[g][e];
-        float fe;
-        if constexpr (GR::kOn) {
-          // same products, in the same order, as eq_from_rec
-          const int nphi = DIM == 2 ? QP * QP : QP;
-          const int k = pop >= nphi ? pop - nphi : pop;
-          const float a = sm.rbuf[(DIM == 2 ? k % QP : k) - GR::a0(g0)][e];
-          const float ab = DIM == 2 ? a * sm.rbuf[GR::kB][e] : a;
-          fe = pop >= nphi ? sm.rbuf[GR::kC][e] * ab : ab;
-        } else {
-          fe = eq_from_rec<DIM, QP, QC>(rbase + goff[j], N, pop);
+        for (int j = 0; j + 1 < J; j += 2) {
+          const bool ok0 = goff[j] >= 0, ok1 = goff[j + 1] >= 0;
+          const int e0 = tid + j * NT;
+          const int e1 = (j + 2) * NT > NST ? min(tid + (j + 1) * NT, NST - 1) : tid + (j + 1) * NT;
+          const float2 v = make_float2(sm.raw[g][e0], sm.raw[g][e1]);
+          float2 fe = make_float2(sm.rbuf[ia][e0], sm.rbuf[ia][e1]);
+          if constexpr (DIM == 2)
+            fe = __fmul2_rn(fe, make_float2(sm.rbuf[GR::kB][e0], sm.rbuf[GR::kB][e1]));
+          if (chi) fe = __fmul2_rn(make_float2(sm.rbuf[GR::kC][e0], sm.rbuf[GR::kC][e1]), fe);
+          const float2 d = sub2(v, fe);
+          const float2 w = STAGE == kStage3 ? __ffma2_rn(f2s(arelax), d, fe)
+                                            : __ffma2_rn(f2s(-arelax), d, v);
+          if (ok0) keep(g, j, w.x, d.x, v.x);
+          if (ok1) keep(g, j + 1, w.y, d.y, v.y);
         }
-        const float d = v - fe;
-        // stage 3: F2 = E0 + c2 D; stages 4, final: F = R - a_ii e_i (R - F_eq)
-        const float w = STAGE == kStage3 ? fmaf(arelax, d, fe) : fmaf(-arelax, d, v);
-        (&sm.tile[g][0][0])[soff[j]] = w;
-        if (oidx[j] >= 0) {
-          sm.ownd[g][oidx[j]] = d;
-          if (STAGE == kStage3) sm.ownv[g][oidx[j]] = v;
+        if constexpr (J % 2 == 1) {
+          constexpr int j = J - 1;
+          if (goff[j] >= 0) {
+            const int e = tid + j * NT;
+            const float v = sm.raw[g][e];
+            float fe = sm.rbuf[ia][e];
+            if constexpr (DIM == 2) fe = __fmul_rn(fe, sm.rbuf[GR::kB][e]);
+            if (chi) fe = __fmul_rn(sm.rbuf[GR::kC][e], fe);
+            const float d = __fsub_rn(v, fe);
+            keep(g, j, STAGE == kStage3 ? fmaf(arelax, d, fe) : fmaf(-arelax, d, v), d, v);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          if (goff[j] < 0) continue;
+          const float v = sm.raw[g][tid + j * NT];
+          const float fe = eq_from_rec<DIM, QP, QC>(rbase + goff[j], N, pop);
+          const float d = __fsub_rn(v, fe);
+          keep(g, j, STAGE == kStage3 ? fmaf(arelax, d, fe) : fmaf(-arelax, d, v), d, v);
         }
       }
     }
