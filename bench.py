@@ -70,10 +70,10 @@ BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
 # profiles/stage_kernel_mixed_quadrant512.md, valid for the kernel sources
 # whose SHA-256 (over STAGE_KERNEL_SOURCES, in that order) is recorded here;
 # reported as null once those sources differ.
-TRAFFIC_SRC_SHA256 = "f0b7ddef3e09d13a898de9ac5a8bfcc76d21f472daba6fcefb6ad2d78c62faf7"
+TRAFFIC_SRC_SHA256 = "abe040b024d5105c33bd86d54a5fb96aec442a724ecdded2332408601da65a2f"
 TRAFFIC_BYTES = {
-    "fp64": {"stage3": 3182717696, "stage4": 2340981760, "final": 1574245632},
-    "mixed": {"stage3": 531635712, "stage4": 669009408, "final": 421227520},
+    "fp64": {"stage3": 3183412224, "stage4": 2342743552, "final": 1573559040},
+    "mixed": {"stage3": 540991744, "stage4": 674020352, "final": 425296128},
 }
 
 

@@ -222,27 +222,31 @@ __device__ __forceinline__ float minmod4f(float a, float b, float c, float d) {
   return lo > 0.0f ? lo : (hi < 0.0f ? hi : 0.0f);
 }
 
+// As in the binary64 face, the bounds and a are formed at twice their value
+// (doubling the stencil's coefficients is exact), so that each bound takes
+// one operation and the final halving folds into one fma.
 __device__ __forceinline__ float mp9_face_fp32(const Mp9LineF& L, float& c1_out, float& dmp_out) {
   const float* d = L.d;
-  float a = (-4.0f / 2520.0f) * d[0];
-  a = fmaf(37.0f / 2520.0f, d[1], a);
-  a = fmaf(-162.0f / 2520.0f, d[2], a);
-  a = fmaf(479.0f / 2520.0f, d[3], a);
-  a = fmaf(1120.0f / 2520.0f, d[4], a);
-  a = fmaf(-255.0f / 2520.0f, d[5], a);
-  a = fmaf(50.0f / 2520.0f, d[6], a);
-  a = fmaf(-5.0f / 2520.0f, d[7], a);
+  float a2 = (2.0f * (-4.0f / 2520.0f)) * d[0];
+  a2 = fmaf(2.0f * (37.0f / 2520.0f), d[1], a2);
+  a2 = fmaf(2.0f * (-162.0f / 2520.0f), d[2], a2);
+  a2 = fmaf(2.0f * (479.0f / 2520.0f), d[3], a2);
+  a2 = fmaf(2.0f * (1120.0f / 2520.0f), d[4], a2);
+  a2 = fmaf(2.0f * (-255.0f / 2520.0f), d[5], a2);
+  a2 = fmaf(2.0f * (50.0f / 2520.0f), d[6], a2);
+  a2 = fmaf(2.0f * (-5.0f / 2520.0f), d[7], a2);
   const float c1 = d[5] - d[4];
   const float c0 = L.c0;
   const float dmp = minmod4f(fmaf(4.0f, c0, -c1), fmaf(4.0f, c1, -c0), c0, c1);
-  const float md = 0.5f * (d[4] - dmp);
-  const float ul = 4.0f * d[3];
-  const float lc = fmaf(4.0f / 3.0f, L.dmm, 0.5f * d[3]);
-  const float lo = fmaxf(fmin3f(0.0f, d[4], md), fmin3f(0.0f, ul, lc));
-  const float hi = fminf(fmax3f(0.0f, d[4], md), fmax3f(0.0f, ul, lc));
+  const float d0_2 = 2.0f * d[4];
+  const float md2 = d[4] - dmp;
+  const float ul2 = 8.0f * d[3];
+  const float lc2 = fmaf(2.0f * (4.0f / 3.0f), L.dmm, d[3]);
+  const float lo2 = fmaxf(fmin3f(0.0f, d0_2, md2), fmin3f(0.0f, ul2, lc2));
+  const float hi2 = fminf(fmax3f(0.0f, d0_2, md2), fmax3f(0.0f, ul2, lc2));
   c1_out = c1;
   dmp_out = dmp;
-  return L.fs[0] + fminf(fmaxf(a, lo), hi);
+  return fmaf(0.5f, fminf(fmaxf(a2, lo2), hi2), L.fs[0]);
 }
 
 template <int NSTEP>

@@ -38,3 +38,10 @@ extern "C" void mp9_line_march8(const double* ext, int n, int sgn, double* out) 
 
 // bits of the device's one-operation DM = minmod4(4a - b, 4b - a, a, b)
 extern "C" long long mp9_dm_bits(double a, double b) { return fdlb::dm_bits(a, b); }
+
+// the binary32 interface value of the window v9 = F_{s-4..s+4}
+extern "C" float mp9_face_f32(const float* v9) {
+  float out = 0.0f;
+  fdlb::mp9_march_fp32<1>(v9 + 4, 1, &out, 1);
+  return out;
+}

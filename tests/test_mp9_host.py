@@ -28,6 +28,8 @@ def mp9():
     lib.mp9_face.restype = ctypes.c_double
     lib.mp9_line.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
     lib.mp9_line_march8.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
+    lib.mp9_face_f32.argtypes = [ctypes.POINTER(ctypes.c_float)]
+    lib.mp9_face_f32.restype = ctypes.c_float
     lib.mp9_dm_bits.argtypes = [ctypes.c_double, ctypes.c_double]
     lib.mp9_dm_bits.restype = ctypes.c_longlong
     return lib
@@ -69,6 +71,24 @@ def test_face_matches_oracle(oracle, mp9):
         scale = np.abs(v).max()
         assert abs(got - want) <= 4e-15 * max(scale, 1e-300), (v, got, want)
     assert nlim > 2000  # the limited branch is exercised
+
+
+def test_binary32_face_matches_oracle(oracle, mp9):
+    """The binary32 face of the mixed-precision path (bounds at twice their
+    value, three-input min/max) against the oracle's binary64 Sec. IV
+    formulas on the same binary32 windows: the limiter is continuous in its
+    inputs, so the two agree to a few binary32 roundings of the window's
+    scale, in both branches."""
+    rng = np.random.default_rng(3)
+    nlim = 0
+    for v in windows(rng, 20000):
+        v32 = np.ascontiguousarray(v, dtype=np.float32)
+        want, lim = oracle.mp9_face(v32.astype(np.float64))
+        nlim += lim
+        got = mp9.mp9_face_f32(v32.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        scale = float(np.abs(v32).max())
+        assert abs(got - want) <= 2e-6 * max(scale, 1e-30), (v32, got, want)
+    assert nlim > 2000
 
 
 def test_hand_examples(mp9):
