@@ -68,9 +68,9 @@ BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # the ncu captures summarised in profiles/stage_kernel_fp64_quadrant512.md and
 # profiles/stage_kernel_mixed_quadrant512.md, valid for the kernel sources
-# whose SHA-256 (over STAGE_KERNEL_SOURCES, in that order) is recorded here;
-# reported as null once those sources differ.
-TRAFFIC_SRC_SHA256 = "abe040b024d5105c33bd86d54a5fb96aec442a724ecdded2332408601da65a2f"
+# whose SHA-256 (over STAGE_KERNEL_SOURCES in that order, comments removed) is
+# recorded here; reported as null once that code differs.
+TRAFFIC_SRC_SHA256 = "05370e8544f66e1abfddb920a74f5b85f2285b1597018fd76a0a09e90d21730b"
 TRAFFIC_BYTES = {
     "fp64": {"stage3": 3183412224, "stage4": 2342743552, "final": 1573559040},
     "mixed": {"stage3": 540991744, "stage4": 674020352, "final": 425296128},
@@ -82,12 +82,18 @@ STAGE_KERNEL_SOURCES = ("fdlb_device.cuh", "fdlb_internal.h", "fdlb_kernels.cu",
                         "fdlb_mp9.cuh")
 
 
-def _kernel_sources_sha256():
+def _kernel_sources_sha256(root=None):
+    """SHA-256 of the stage kernels' sources with // comments and blank lines
+    removed, so that a comment edit keeps the recorded traffic."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for name in STAGE_KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1909_08390_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(root or ROOT, "paper_1909_08390_gb300", "csrc", name)) as f:
+            for line in f:
+                code = re.sub(r"//.*", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()
 
 

@@ -208,9 +208,10 @@ __device__ __forceinline__ float sfma(float a, float b, float c) { return fmaf(a
 // Moment sums of binary32 populations, kept as unevaluated binary32 pairs
 // (hi + lo) with error-free transformations: TwoSum for each addition and the
 // fma-exact product error for p * v with p = hi + lo split on the host.  The
-// pairs carry about 44 significant bits and are folded into binary64 once per
-// cell, so n, u and T = (E - n u^2)/((D+K) n) are recovered at binary64
-// accuracy although the populations are binary32.
+// pairs carry about 44 significant bits, so n, u and T = (E - n u^2)/((D+K) n)
+// are recovered without the cancellation's loss although the populations are
+// binary32: the stage kernels go on in pair arithmetic (fdlb_mixed.cu), the
+// moments output folds the pairs into binary64 once per cell.
 struct MomentsF {
   float nh, nl, jxh, jxl, jyh, jyl, eh, el;
 };

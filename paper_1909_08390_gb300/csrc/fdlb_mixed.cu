@@ -7,9 +7,9 @@
 // applied by the kernel of stage i+1, when it loads the advected array:
 //   * every kernel writes the unrelaxed explicit part R_i of its stage, sums
 //     the moments of R_i per cell (Eq. Moments_discrete, compensated binary32
-//     pairs folded into binary64), and stores a record of the cell's
-//     equilibrium factors (Eq. gExpanded, binary64 arithmetic rounded once to
-//     binary32);
+//     pairs), and stores a record of the cell's equilibrium factors
+//     (Eq. gExpanded, in binary32-pair arithmetic of about 48 significant
+//     bits, each factor rounded once to binary32);
 //   * the next kernel forms the relaxed values from R_i and the record as it
 //     stages the tile and its halo (Sec. III closed forms):
 //       stage 3 stages F2 = E0 + c2 (F^n - E0) from F^n,
