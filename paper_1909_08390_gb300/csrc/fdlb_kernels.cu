@@ -13,7 +13,10 @@
 //           accumulators in the output arrays;
 //   pass 2  per cell: n, u, T from the moments, the Hermite equilibrium
 //           factors (Eq. gExpanded, recurrence form), and the closed-form
-//           implicit BGK relaxation of every population (Sec. III).
+//           implicit BGK relaxation of every population (Sec. III).  Stage 3
+//           leaves D3 = R3 - F_eq(R3) in the array D, which the stage-4
+//           kernel folds into A4 and A_fin in its pass 1, so that stage 3's
+//           pass 2 rewrites two arrays instead of three.
 // The flux itself never goes to global memory.
 #include "fdlb_device.cuh"
 
@@ -167,9 +170,11 @@ __device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, i
             A4[e] = sfma(-sc.at42, X, sfma(-sc.k4, dd, f));
             Af[e] = sfma(-sc.wt2, X, sfma(-sc.kf, dd, f));
           } else if (STAGE == kStage4) {
-            R = sfma(-sc.at43, X, A4[e]);
+            // the D3 terms of A4 and A_fin, left by stage 3 in D
+            const S d3 = Dn[e];
+            R = sfma(-sc.at43, X, sfma(-sc.a43e3, d3, A4[e]));
             A4[e] = R;
-            Af[e] = sfma(-sc.wt3, X, Af[e]);
+            Af[e] = sfma(-sc.wt3, X, sfma(-sc.w3e3, d3, Af[e]));
           } else {  // kFinal: F^{n+1}
             R = sfma(-sc.wt4, X, Af[e]);
             F[e] = R;
@@ -200,11 +205,12 @@ __device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, i
       const int64_t e = pop * N + c;
       const S fe = feq_of<DIM, QP, QC, S>(eq, pop);
       if (STAGE == kStage3) {
+        // F3 relaxed; D3 goes to D (free until the final stage rewrites it),
+        // and stage 4 applies its terms to A4 and A_fin as it reads them
         const S R = F3[e];
         const S D3 = R - fe;
         F3[e] = sfma(-sc.a33e3, D3, R);
-        A4[e] = sfma(-sc.a43e3, D3, A4[e]);
-        Af[e] = sfma(-sc.w3e3, D3, Af[e]);
+        Dn[e] = D3;
       } else if (STAGE == kStage4) {
         const S R = A4[e];
         const S D4 = R - fe;

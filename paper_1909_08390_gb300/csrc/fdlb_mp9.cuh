@@ -216,10 +216,12 @@ __device__ __forceinline__ float fmax3f(float a, float b, float c) {
 #endif
 }
 
+// minmod4: the smallest of four positive values, the largest of four
+// negative ones, else 0; that is max(min, 0) + min(max, 0).
 __device__ __forceinline__ float minmod4f(float a, float b, float c, float d) {
   const float lo = fmin3f(a, b, fminf(c, d));
   const float hi = fmax3f(a, b, fmaxf(c, d));
-  return lo > 0.0f ? lo : (hi < 0.0f ? hi : 0.0f);
+  return fmaxf(lo, 0.0f) + fminf(hi, 0.0f);
 }
 
 // As in the binary64 face, the bounds and a are formed at twice their value
