@@ -39,10 +39,10 @@ UNIT = "cell-velocity updates/s"
 # kernel (FMA = 2): two MP-9 interface values per population (x and y), each
 # 17 (9-point F^L) + 2 (differences) + 2 (F^MP) + 3 (limiter test) = 24; the
 # flux difference 5; the stage's explicit part, moments and relaxation
-# (stage 3: 12 + 4 + 4; stage 4: 8 + 4 + 6, its explicit part taking stage
-# 3's D3 terms; final: 2 + 4 + 4).  The limited MP branch, divisions and
-# per-cell equilibrium factors are not counted.
-FLOPS_PER_POP = {"stage3": 48 + 5 + 20, "stage4": 48 + 5 + 18, "final": 48 + 5 + 10}
+# (stage 3: 12 + 4 + 4; stage 4: 8 + 4 + 4 and final: 4 + 4 + 4, their
+# explicit parts taking the previous stage's D_i terms).  The limited MP
+# branch, divisions and per-cell equilibrium factors are not counted.
+FLOPS_PER_POP = {"stage3": 48 + 5 + 20, "stage4": 48 + 5 + 16, "final": 48 + 5 + 12}
 # The kernels are bound by GB300's binary64 pipe, which executes one add,
 # multiply or fused multiply-add per lane slot (2 slots per SM and clock), so
 # the roofline counts binary64 operations, not flops.  Algorithmic operations
@@ -50,14 +50,14 @@ FLOPS_PER_POP = {"stage3": 48 + 5 + 20, "stage4": 48 + 5 + 18, "final": 48 + 5 +
 # each (the new difference, the 8-term stencil, the curvature, the two DM
 # candidates, the MD and LC bounds, the clamped result); the flux difference 4
 # (two differences, a multiply, an fma); then the stage's explicit part,
-# moment sums and relaxation: stage 3 6 + 4 + 3, stage 4 4 + 4 + 4, final
-# 1 + 4 + 3.  The tiles' extra interface per line, the per-cell equilibrium
+# moment sums and relaxation: stage 3 6 + 4 + 3, stage 4 4 + 4 + 3, final
+# 2 + 4 + 3.  The tiles' extra interface per line, the per-cell equilibrium
 # factors and divisions are not counted.
-FP64_OPS_PER_POP = {"stage3": 30 + 4 + 13, "stage4": 30 + 4 + 12, "final": 30 + 4 + 8}
+FP64_OPS_PER_POP = {"stage3": 30 + 4 + 13, "stage4": 30 + 4 + 11, "final": 30 + 4 + 9}
 # Algorithmic HBM bytes per population and launch (binary64): arrays read and
 # written once each by the kernel (stage 3: F2, F, D -> F3, A4, Af, D3;
-# stage 4: F3, A4, Af, D3 -> A4, Af; final: A4, Af -> F, D, F2).
-BYTES_PER_POP = {"stage3": 7 * 8, "stage4": 6 * 8, "final": 5 * 8}
+# stage 4: F3, A4, Af, D3 -> F4, Af, D4; final: F4, Af, D4 -> F, D, F2).
+BYTES_PER_POP = {"stage3": 7 * 8, "stage4": 7 * 8, "final": 6 * 8}
 # Mixed precision (single-pass kernels, 4 B per population): stage 3 reads
 # F^n and writes R3, A4', Af'; stage 4 reads R3, A4', Af' and writes R4, Af'';
 # the final stage reads R4, Af'' and writes F^{n+1}; plus, per cell, one

@@ -13,10 +13,10 @@
 //           accumulators in the output arrays;
 //   pass 2  per cell: n, u, T from the moments, the Hermite equilibrium
 //           factors (Eq. gExpanded, recurrence form), and the closed-form
-//           implicit BGK relaxation of every population (Sec. III).  Stage 3
-//           leaves D3 = R3 - F_eq(R3) in the array D, which the stage-4
-//           kernel folds into A4 and A_fin in its pass 1, so that stage 3's
-//           pass 2 rewrites two arrays instead of three.
+//           implicit BGK relaxation of every population (Sec. III).  Stages
+//           3 and 4 leave D_i = R_i - F_eq(R_i) in the array D, which the
+//           next kernel folds into A4 and A_fin in its pass 1, so that pass 2
+//           rewrites the relaxed populations and D only.
 // The flux itself never goes to global memory.
 #include "fdlb_device.cuh"
 
@@ -175,8 +175,8 @@ __device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, i
             R = sfma(-sc.at43, X, sfma(-sc.a43e3, d3, A4[e]));
             A4[e] = R;
             Af[e] = sfma(-sc.wt3, X, sfma(-sc.w3e3, d3, Af[e]));
-          } else {  // kFinal: F^{n+1}
-            R = sfma(-sc.wt4, X, Af[e]);
+          } else {  // kFinal: F^{n+1}, with the D4 term left by stage 4 in D
+            R = sfma(-sc.wt4, X, sfma(-sc.w4e4, Dn[e], Af[e]));
             F[e] = R;
           }
           accumulate<DIM, QP, QC>(p, mom[k], pop, R);
@@ -212,10 +212,11 @@ __device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, i
         F3[e] = sfma(-sc.a33e3, D3, R);
         Dn[e] = D3;
       } else if (STAGE == kStage4) {
+        // F4 relaxed; D4 goes to D for the final stage's A_fin
         const S R = A4[e];
         const S D4 = R - fe;
         A4[e] = sfma(-sc.a44e4, D4, R);
-        Af[e] = sfma(-sc.w4e4, D4, Af[e]);
+        Dn[e] = D4;
       } else {  // kPrep / kFinal: D and F2 of the new state
         const S f = F[e];
         const S dd = f - fe;
