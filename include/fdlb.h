@@ -235,7 +235,9 @@ int fdlb_forward_ckpt(fdlb_ctx* ctx, int64_t nsteps, int every, void* ckpt);
  * stored: Fbar (device, state layout) holds dLoss/dF(nsteps) on entry and
  * dLoss/dF(0) on return; dparams (host, 2) receives the step contributions
  * dLoss/dgamma and dLoss/dtau.  The context's state is left as it was.
- * Allocates its work space (4 every + 9 states) on first use; the context's
+ * Allocates its work space (8 every + 13 states: two segment buffers, so
+ * that one segment's recompute overlaps the previous segment's adjoint on a
+ * second stream the call creates and destroys) on first use; the context's
  * derived scratch arrays are rebuilt from its state before it returns. */
 int fdlb_adjoint(fdlb_ctx* ctx, int64_t nsteps, int every, const void* ckpt, double* Fbar,
                  double* dparams);

@@ -876,10 +876,11 @@ int fdlb_adjoint(fdlb_ctx* c, int64_t nsteps, int every, const void* ckpt, doubl
   if (!adjoint_lattice(c))
     return fdlb::ctx_error(c, FDLB_EINVAL, "the adjoint covers 1-D binary64 outlet contexts");
   const size_t bytes = fdlb_state_bytes(c);
-  // work space: per step of a segment the saved F^n, F2, F3 and F4 (one more
-  // slot for the state after the segment's last step), 5 adjoint arrays and
-  // the scalar accumulators
-  const size_t need = (size_t)(4 * every + 4 + 5) * bytes + 256;
+  // work space: two segment buffers, each holding per step of a segment the
+  // saved F^n, F2, F3 and F4 (one more slot for the state after the
+  // segment's last step); 5 adjoint arrays; the scalar accumulators
+  const size_t seg_states = (size_t)(4 * every + 4);
+  const size_t need = (2 * seg_states + 5) * bytes + 256;
   if (c->adj_bytes < need) {
     if (c->adj_buf) cudaFree(c->adj_buf);
     c->adj_buf = nullptr;
@@ -889,53 +890,79 @@ int fdlb_adjoint(fdlb_ctx* c, int64_t nsteps, int every, const void* ckpt, doubl
     c->adj_bytes = need;
   }
   char* w = (char*)c->adj_buf;
-  auto slot = [&](int64_t k, int which) { return (double*)(w + ((size_t)k * 4 + which) * bytes); };
-  double* A4b = slot(every + 1, 0);
+  auto slot = [&](int buf, int64_t k, int which) {
+    return (double*)(w + (buf * seg_states + (size_t)k * 4 + which) * bytes);
+  };
+  double* A4b = (double*)(w + 2 * seg_states * bytes);
   double* X3b = A4b + bytes / 8;
   double* X2b = X3b + bytes / 8;
   double* Fpt = X2b + bytes / 8;
   double* Db = Fpt + bytes / 8;
   double* scal = Db + bytes / 8;
   cudaStream_t s = c->stream;
-  cudaError_t e = cudaMemsetAsync(scal, 0, fdlb::kNumAdjScalars * sizeof(double), s);
+  // The segments are processed last first.  Each segment's forward states are
+  // recomputed from its checkpoint on a second stream, into the buffer the
+  // adjoint of the segment after it no longer reads, while that adjoint runs:
+  // both are chains of small launches that leave most of the GPU idle, so
+  // they overlap.  Events order a segment's adjoint after its recompute, and
+  // a buffer's recompute after the adjoint that last read it.
+  cudaStream_t rs = nullptr;
+  cudaEvent_t ev_start = nullptr, rdone[2] = {nullptr, nullptr}, adone[2] = {nullptr, nullptr};
+  bool aused[2] = {false, false};
+  cudaError_t e = cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&rdone[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&adone[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, fdlb::kNumAdjScalars * sizeof(double), s);
+  // the recompute stream starts after everything already queued on s
+  if (e == cudaSuccess) e = cudaEventRecord(ev_start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, ev_start, 0);
   const int64_t nseg = (nsteps + every - 1) / every;
   for (int64_t sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
+    const int b = (int)(sg & 1);
     const int64_t s0 = sg * every;
     const int64_t ns = (nsteps - s0 < every) ? nsteps - s0 : every;
     // recompute the segment from its checkpoint: every launch gets its own
     // array pointers, so the stage kernels leave F^n, F2, F3 and F4 of each
     // step in its slot (the final stage writes F^{n+1} and its F2 into the
-    // next slot); D and Af are the context's own scratch arrays
-    e = cudaMemcpyAsync(slot(0, 0), (const char*)ckpt + sg * bytes, bytes,
-                        cudaMemcpyDeviceToDevice, s);
+    // next slot); D and Af are the context's own scratch arrays, used by
+    // the recomputes alone
+    if (aused[b]) e = cudaStreamWaitEvent(rs, adone[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(slot(b, 0, 0), (const char*)ckpt + sg * bytes, bytes,
+                          cudaMemcpyDeviceToDevice, rs);
     int le = 0;
     if (e == cudaSuccess) {
       DevParams q = c->dp;
-      q.F = slot(0, 0);
-      q.F2 = slot(0, 1);
-      le = fdlb::launch_stage(q, fdlb::kPrep, s);
+      q.F = slot(b, 0, 0);
+      q.F2 = slot(b, 0, 1);
+      le = fdlb::launch_stage(q, fdlb::kPrep, rs);
     }
     for (int64_t k = 0; k < ns && e == cudaSuccess && !le; ++k) {
       DevParams q = c->dp;
-      q.F = slot(k, 0);
-      q.F2 = slot(k, 1);
-      q.F3 = slot(k, 2);
-      q.A4 = slot(k, 3);
-      le = fdlb::launch_stage(q, fdlb::kStage3, s);
-      if (!le) le = fdlb::launch_stage(q, fdlb::kStage4, s);
-      q.F = slot(k + 1, 0);
-      q.F2 = slot(k + 1, 1);
-      if (!le) le = fdlb::launch_stage(q, fdlb::kFinal, s);
+      q.F = slot(b, k, 0);
+      q.F2 = slot(b, k, 1);
+      q.F3 = slot(b, k, 2);
+      q.A4 = slot(b, k, 3);
+      le = fdlb::launch_stage(q, fdlb::kStage3, rs);
+      if (!le) le = fdlb::launch_stage(q, fdlb::kStage4, rs);
+      q.F = slot(b, k + 1, 0);
+      q.F2 = slot(b, k + 1, 1);
+      if (!le) le = fdlb::launch_stage(q, fdlb::kFinal, rs);
     }
     if (le) e = (cudaError_t)le;
+    if (e == cudaSuccess) e = cudaEventRecord(rdone[b], rs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, rdone[b], 0);
     // adjoint steps of the segment, last step first; Fbar is updated in
     // place (the stage-2 adjoint reads no adjoint of F^{n+1})
     for (int64_t k = ns - 1; k >= 0 && e == cudaSuccess; --k) {
       fdlb::AdjParams a{};
-      a.Fn = slot(k, 0);
-      a.F2s = slot(k, 1);
-      a.F3s = slot(k, 2);
-      a.F4s = slot(k, 3);
+      a.Fn = slot(b, k, 0);
+      a.F2s = slot(b, k, 1);
+      a.F3s = slot(b, k, 2);
+      a.F4s = slot(b, k, 3);
       a.Gbar = Fbar;
       a.A4bar = A4b;
       a.X3bar = X3b;
@@ -949,10 +976,31 @@ int fdlb_adjoint(fdlb_ctx* c, int64_t nsteps, int every, const void* ckpt, doubl
       if (!r) r = launch_adj_any(2, c->dp, a, s);
       if (r) e = (cudaError_t)r;
     }
+    if (e == cudaSuccess) e = cudaEventRecord(adone[b], s);
+    aused[b] = true;
+  }
+  // s has waited for every recompute it used; let it also cover the stream's
+  // tail before the stream goes away
+  if (rs) {
+    cudaEvent_t tail = nullptr;
+    if (cudaEventCreateWithFlags(&tail, cudaEventDisableTiming) == cudaSuccess) {
+      if (cudaEventRecord(tail, rs) == cudaSuccess) cudaStreamWaitEvent(s, tail, 0);
+      cudaEventDestroy(tail);
+    }
   }
   double h[fdlb::kNumAdjScalars] = {0};
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, scal, sizeof h, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  const cudaError_t es = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = es;
+  for (int i = 0; i < 2; ++i) {
+    if (rdone[i]) cudaEventDestroy(rdone[i]);
+    if (adone[i]) cudaEventDestroy(adone[i]);
+  }
+  if (ev_start) cudaEventDestroy(ev_start);
+  if (rs) {
+    cudaStreamSynchronize(rs);
+    cudaStreamDestroy(rs);
+  }
   if (e != cudaSuccess) return fdlb::ctx_error(c, FDLB_ECUDA, cudaGetErrorString(e));
   // the context's D and Af scratch arrays were overwritten: derive them anew
   c->prepared = false;
