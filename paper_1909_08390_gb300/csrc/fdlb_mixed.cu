@@ -598,7 +598,7 @@ __global__ void __launch_bounds__(TileCfg<DIM, VAR>::NT, DIM == 2 ? 4 : (TileCfg
 }
 
 template <int QP, int QC, int STAGE, int VAR>
-__global__ void __launch_bounds__(TileCfg<1, VAR>::NT, 4)
+__global__ void __launch_bounds__(TileCfg<1, VAR>::NT, 6)
     mixed_batch_kernel(const __grid_constant__ DevParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   auto& sm = *reinterpret_cast<MixSmem<1, QP, QC, VAR>*>(smraw);
