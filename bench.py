@@ -71,10 +71,10 @@ BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
 # profiles/stage_kernel_mixed_quadrant512.md, valid for the kernel sources
 # whose SHA-256 (over STAGE_KERNEL_SOURCES in that order, comments removed) is
 # recorded here; reported as null once that code differs.
-TRAFFIC_SRC_SHA256 = "44dcc3f7b9a43ee3b21e7e7b68a471e3c0f9f243a0ac380c5049328c2401b0e0"
+TRAFFIC_SRC_SHA256 = "e20554ba54ed01e9ee07376ab1f97caec15456fce8bb4c2af227a364608506a2"
 TRAFFIC_BYTES = {
-    "fp64": {"stage3": 2375250944, "stage4": 2355373568, "final": 1845685504},
-    "mixed": {"stage3": 541015296, "stage4": 673335808, "final": 424664832},
+    "fp64": {"stage3": 2378509056, "stage4": 2355162624, "final": 1847106560},
+    "mixed": {"stage3": 540218880, "stage4": 673586944, "final": 424611072},
 }
 
 
