@@ -60,10 +60,10 @@ FP64_OPS_PER_POP = {"stage3": 30 + 4 + 13, "stage4": 30 + 4 + 11, "final": 30 + 
 BYTES_PER_POP = {"stage3": 7 * 8, "stage4": 7 * 8, "final": 6 * 8}
 # Mixed precision (single-pass kernels, 4 B per population): stage 3 reads
 # F^n and writes R3, A4', Af'; stage 4 reads R3, A4', Af' and writes R4, Af'';
-# the final stage reads R4, Af'' and writes F^{n+1}; plus, per cell, one
-# equilibrium record read and one written (17 binary32 values for the 8x8
-# lattice: 2 * 17 * 4 / 128 B per population).
-MIXED_RECORD_BYTES_PER_POP = 2 * 17 * 4 / 128
+# the final stage reads R4, Af'' and writes F^{n+1}; plus, per cell, the
+# equilibrium record's components read (24: A, B and C B) and written (25, C
+# too) for the 8x8 lattice: (24 + 25) * 4 / 128 B per population.
+MIXED_RECORD_BYTES_PER_POP = (24 + 25) * 4 / 128
 BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
                        for k, n in (("stage3", 4), ("stage4", 5), ("final", 3))}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from

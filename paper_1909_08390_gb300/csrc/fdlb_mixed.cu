@@ -28,11 +28,16 @@ namespace {
 // Components of a cell's record.  phi^eq(kx, ky) = A[kx] * B[ky] with
 // A = n g_x, B = g_y (1-D: A[k]); chi^eq(qx, qy) = C * A[qx] * B[qy] with
 // C = (D+K-d) T when Qchi = Qphi, else Hx[qx] * Hy[qy] with Hx = nchi h_x.
+// 2-D records with Qchi = Qphi also hold CB[ky] = C B[ky] (each rounded once),
+// so that chi^eq = A[qx] * CB[qy] takes the same two factors as phi^eq.
 template <int DIM, int QP, int QC>
 struct RecLayout {
   static constexpr bool kSame = QP == QC;
   static constexpr int kChi = DIM == 1 ? QP : 2 * QP;  // first chi component
-  static constexpr int W = kSame ? kChi + 1 : kChi + (DIM == 1 ? QC : 2 * QC);
+  static constexpr bool kCB = DIM == 2 && kSame;
+  static constexpr int kCBo = kChi + 1;               // first CB component
+  static constexpr int W = kSame ? kChi + 1 + (kCB ? QP : 0) : kChi + (DIM == 1 ? QC : 2 * QC);
+  static_assert(!kCB || kCBo + QP == W, "CB components close the record");
 };
 
 // Equilibrium of population pop from a record whose components lie `stride`
@@ -188,6 +193,10 @@ __device__ __forceinline__ void write_record(const DevParams& p, DF kchi, DF n, 
   const DF kT = df_mul(kchi, T);
   if constexpr (R::kSame) {
     rec[R::kChi * N + cell] = df_round(kT);
+    if constexpr (R::kCB) {  // g holds the y factors B
+#pragma unroll
+      for (int k = 0; k < QP; ++k) rec[(R::kCBo + k) * N + cell] = df_round(df_mul(kT, g[k]));
+    }
   } else {
     DF h[QC];
     axis_g_df<QC>(p.wHch, p.wHcl, ux, T, df_mul(kT, n), h);
@@ -235,16 +244,15 @@ __device__ __forceinline__ void finish_cell(const DevParams& p, DF kchi, DF invD
 // whose groups align with rows of the velocity grid ((8, 8) with groups of 4
 // in 2-D; groups of 8 or 16 in 1-D).  Slot s of the group's buffer holds one
 // record component: slots 0..NA-1 the x factors A of the group's columns,
-// then (2-D) the y factor B of its row, then the chi factor C.
+// then slot kB the second factor: in 2-D B of the group's row (phi) or CB
+// (chi), in 1-D the chi factor C.
 template <int DIM, int QP, int QC, int G>
 struct GroupRec {
   static constexpr bool kOn =
       QP == QC && (DIM == 2 ? (QP % G == 0) : (QP % G == 0 || G % QP == 0));
   static constexpr int NA = G < QP ? G : QP;
   static constexpr int kB = NA;
-  static constexpr int kC = NA + (DIM == 2 ? 1 : 0);
-  static constexpr int NS = kC + 1;
-  static_assert(kB <= kC, "slot order");
+  static constexpr int NS = kB + 1;
   // first x-factor component of group g0 (1-D groups of 2 QP start at 0)
   __device__ static int a0(int g0) {
     const int nphi = DIM == 2 ? QP * QP : QP;
@@ -255,47 +263,51 @@ struct GroupRec {
   // record component held by slot s for group g0 (-1: unused)
   __device__ static int comp(int g0, int s) {
     const int nphi = DIM == 2 ? QP * QP : QP;
+    using R = RecLayout<DIM, QP, QC>;
     if (s < NA) return a0(g0) + s;
-    if (DIM == 2 && s == kB) return QP + (g0 >= nphi ? g0 - nphi : g0) / QP;
-    return has_chi(g0) ? RecLayout<DIM, QP, QC>::kChi : -1;
+    if (DIM == 2) return (g0 >= nphi ? R::kCBo + (g0 - nphi) / QP : QP + g0 / QP);
+    return has_chi(g0) ? R::kChi : -1;
   }
 };
 
-template <int DIM, int QP, int QC, int VAR>
+template <int DIM, int QP, int QC, int VAR, int STAGE>
 struct MixSmem {
   using C = TileCfg<DIM, VAR>;
   static constexpr int SXH = C::TX + 2 * H;             // staged columns
   static constexpr int SX = SXH + (DIM == 2 ? 1 : 0);   // tile row pitch
   static constexpr int SY = DIM == 2 ? C::TY + 2 * H : 1;
-  static constexpr int NST = SY * SXH;                  // staged cells
-  float raw[C::G][NST];                // the group's advected values as loaded
+  // staged cells: tile + halo without the 2-D corner blocks, which feed no
+  // line (rows 0..H-1 and H+TY.. take the tile's columns only)
+  static constexpr int NSC = DIM == 2 ? C::TY * SXH + 2 * H * C::TX : SXH;
+  float raw[C::G][NSC];                // the group's advected values as loaded
   // the group's record components (GroupRec plan), as loaded
   float rbuf[GroupRec<DIM, QP, QC, C::G>::kOn ? GroupRec<DIM, QP, QC, C::G>::NS : 1]
-            [GroupRec<DIM, QP, QC, C::G>::kOn ? NST : 1];
+            [GroupRec<DIM, QP, QC, C::G>::kOn ? NSC : 1];
   float tile[C::G][SY][SX];            // relaxed advected populations
   float hx[C::G][C::TY][C::TX + 1];    // interface values along x
   float hy[DIM == 2 ? C::G : 1][DIM == 2 ? C::TX : 1][C::TY + 1];
-  float ownv[C::G][C::TY * C::TX];     // stage 3: F^n of the own cells
   float ownd[C::G][C::TY * C::TX];     // R - F_eq of the own cells
+  // stage 3 only: F^n of the own cells
+  float ownv[STAGE == kStage3 ? C::G : 1][STAGE == kStage3 ? C::TY * C::TX : 1];
 };
 
 // One tile of one stage.  Ends with every thread past its last use of the
 // shared memory, so a persistent CTA may start its next tile at once.
 template <int DIM, int QP, int QC, int STAGE, int VAR>
 __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, int x0, int y0,
-                                           MixSmem<DIM, QP, QC, VAR>& sm) {
+                                           MixSmem<DIM, QP, QC, VAR, STAGE>& sm) {
   using C = TileCfg<DIM, VAR>;
   using L = Lat<DIM, QP, QC>;
-  using M = MixSmem<DIM, QP, QC, VAR>;
+  using M = MixSmem<DIM, QP, QC, VAR, STAGE>;
   constexpr int TX = C::TX, TY = C::TY, NT = C::NT, G = C::G, SEG = C::SEG;
-  constexpr int SX = M::SX, SXH = M::SXH, NST = M::NST;
+  constexpr int SX = M::SX, SXH = M::SXH, NSC = M::NSC;
   constexpr int CELLS = TX * TY;
   constexpr int CPT = (CELLS + NT - 1) / NT;
   constexpr int NSEG = (TX + 1) / SEG;
   static_assert(NSEG * SEG == TX + 1, "segments tile the line");
   constexpr int NLINE = DIM == 2 ? TX + TY : 1;
   static_assert(G * NLINE * NSEG == NT, "one march task per thread");
-  constexpr int J = (NST + NT - 1) / NT;  // staged cells per thread
+  constexpr int J = (NSC + NT - 1) / NT;  // staged cells per thread
 
   float* __restrict__ const F = (float*)p.F;
   float* __restrict__ const R3 = (float*)p.F3;
@@ -314,13 +326,26 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const int e = tid + j * NT;
-    const int r = e / SXH, c = e % SXH;
+    // staged cell e (NSC of them): 2-D in three blocks -- rows above the tile
+    // (tile columns only), the tile's rows with both side halos, rows below
+    int r, c;
+    if (DIM == 1) {
+      r = 0;
+      c = e;
+    } else if (e < H * TX) {
+      r = e / TX;
+      c = H + e % TX;
+    } else if (e < H * TX + TY * SXH) {
+      r = H + (e - H * TX) / SXH;
+      c = (e - H * TX) % SXH;
+    } else {
+      r = H + TY + (e - H * TX - TY * SXH) / TX;
+      c = H + (e - H * TX - TY * SXH) % TX;
+    }
     soff[j] = r * SX + c;
     goff[j] = -1;
     oidx[j] = -1;
-    // 2-D: the corner blocks of the halo feed no line and are not loaded
-    const bool corner = DIM == 2 && (r < H || r >= H + TY) && (c < H || c >= H + TX);
-    if (e < NST && !corner) {
+    if (e < NSC) {
       const int gx = wrap_or_clamp(x0 - H + c, geo.nx, p.bc);
       const int gy = DIM == 2 ? wrap_or_clamp(y0 - H + r, geo.ny, p.bc) : 0;
       goff[j] = gy * geo.nx + gx;
@@ -419,7 +444,8 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
     }
     // ---- stage the group: relaxed advected values on tile + halo
     cp_async_wait_all();
-    // The equilibrium is A B (phi) or C (A B) (chi) from the record slots,
+    // The equilibrium is A B (phi) or A CB (chi) from the record slots in
+    // 2-D, A (phi) or C A (chi) in 1-D,
     // D = R - F_eq, and stage 3 stages F2 = E0 + c2 D, stages 4 and final
     // F = R - a_ii e_i D; every operation is rounded on its own, so the
     // paired (packed) and single forms below agree bit for bit.
@@ -427,7 +453,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
       (&sm.tile[g][0][0])[soff[j]] = w;
       if (oidx[j] >= 0) {
         sm.ownd[g][oidx[j]] = d;
-        if (STAGE == kStage3) sm.ownv[g][oidx[j]] = v;
+        if constexpr (STAGE == kStage3) sm.ownv[g][oidx[j]] = v;
       }
     };
 #pragma unroll
@@ -446,12 +472,13 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
         for (int j = 0; j + 1 < J; j += 2) {
           const bool ok0 = goff[j] >= 0, ok1 = goff[j + 1] >= 0;
           const int e0 = tid + j * NT;
-          const int e1 = (j + 2) * NT > NST ? min(tid + (j + 1) * NT, NST - 1) : tid + (j + 1) * NT;
+          const int e1 = (j + 2) * NT > NSC ? min(tid + (j + 1) * NT, NSC - 1) : tid + (j + 1) * NT;
           const float2 v = make_float2(sm.raw[g][e0], sm.raw[g][e1]);
           float2 fe = make_float2(sm.rbuf[ia][e0], sm.rbuf[ia][e1]);
           if constexpr (DIM == 2)
             fe = __fmul2_rn(fe, make_float2(sm.rbuf[GR::kB][e0], sm.rbuf[GR::kB][e1]));
-          if (chi) fe = __fmul2_rn(make_float2(sm.rbuf[GR::kC][e0], sm.rbuf[GR::kC][e1]), fe);
+          else if (chi)
+            fe = __fmul2_rn(make_float2(sm.rbuf[GR::kB][e0], sm.rbuf[GR::kB][e1]), fe);
           const float2 d = sub2(v, fe);
           const float2 w = STAGE == kStage3 ? __ffma2_rn(f2s(arelax), d, fe)
                                             : __ffma2_rn(f2s(-arelax), d, v);
@@ -465,7 +492,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
             const float v = sm.raw[g][e];
             float fe = sm.rbuf[ia][e];
             if constexpr (DIM == 2) fe = __fmul_rn(fe, sm.rbuf[GR::kB][e]);
-            if (chi) fe = __fmul_rn(sm.rbuf[GR::kC][e], fe);
+            else if (chi) fe = __fmul_rn(sm.rbuf[GR::kB][e], fe);
             const float d = __fsub_rn(v, fe);
             keep(g, j, STAGE == kStage3 ? fmaf(arelax, d, fe) : fmaf(-arelax, d, v), d, v);
           }
@@ -588,10 +615,12 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
 }
 
 template <int DIM, int QP, int QC, int STAGE, int VAR = 0>
-__global__ void __launch_bounds__(TileCfg<DIM, VAR>::NT, DIM == 2 ? 4 : (TileCfg<DIM, VAR>::NT >= 128 ? 5 : 8))
+__global__ void __launch_bounds__(TileCfg<DIM, VAR>::NT,
+                                  DIM == 2 ? (STAGE == kStage3 ? 4 : 5)
+                                           : (TileCfg<DIM, VAR>::NT >= 128 ? 5 : 8))
     mixed_stage_kernel(const __grid_constant__ DevParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  auto& sm = *reinterpret_cast<MixSmem<DIM, QP, QC, VAR>*>(smraw);
+  auto& sm = *reinterpret_cast<MixSmem<DIM, QP, QC, VAR, STAGE>*>(smraw);
   const Geo geo{p.nx, p.ny, 0, p.kchi, p.invDK, p.dtdx, p.dtdy, -1};
   mixed_tile<DIM, QP, QC, STAGE, VAR>(p, geo, blockIdx.x * TileCfg<DIM, VAR>::TX,
                                       blockIdx.y * TileCfg<DIM, VAR>::TY, sm);
@@ -601,7 +630,7 @@ template <int QP, int QC, int STAGE, int VAR>
 __global__ void __launch_bounds__(TileCfg<1, VAR>::NT, 6)
     mixed_batch_kernel(const __grid_constant__ DevParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  auto& sm = *reinterpret_cast<MixSmem<1, QP, QC, VAR>*>(smraw);
+  auto& sm = *reinterpret_cast<MixSmem<1, QP, QC, VAR, STAGE>*>(smraw);
   for (int w = blockIdx.x; w < p.nwork; w += gridDim.x) {
     const WorkItem it = p.work[w];
     const BatchProblem& bp = p.probs[it.prob];
@@ -641,35 +670,44 @@ __global__ void mixed_prep_kernel(const __grid_constant__ DevParams p) {
   finish_cell<DIM, QP, QC>(p, df_of(geo.kchi), df_of(geo.invDK), geo.prob, m, p.erec[0], c);
 }
 
+template <int DIM, int QP, int QC, int VAR, int STAGE>
+constexpr int smem_bytes() {
+  return (int)sizeof(MixSmem<DIM, QP, QC, VAR, STAGE>);
+}
+
 template <int DIM, int QP, int QC>
 int setup_t() {
   cudaError_t e = cudaSuccess;
-  const int b = (int)sizeof(MixSmem<DIM, QP, QC, 0>);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage3>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<DIM, QP, QC, 0, kStage3>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage4>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<DIM, QP, QC, 0, kStage4>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kFinal>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<DIM, QP, QC, 0, kFinal>());
   return (int)e;
 }
 
 template <int QP, int QC, int VAR>
 int setup_batch_v() {
   cudaError_t e = cudaSuccess;
-  const int b = (int)sizeof(MixSmem<1, QP, QC, VAR>);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mixed_batch_kernel<QP, QC, kStage3, VAR>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<1, QP, QC, VAR, kStage3>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mixed_batch_kernel<QP, QC, kStage4, VAR>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<1, QP, QC, VAR, kStage4>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(mixed_batch_kernel<QP, QC, kFinal, VAR>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<1, QP, QC, VAR, kFinal>());
   return (int)e;
 }
 
@@ -677,11 +715,19 @@ template <int DIM, int QP, int QC, int VAR>
 int launch_tv(const DevParams& p, int stage, cudaStream_t s) {
   using C = TileCfg<DIM, VAR>;
   const dim3 grid((p.nx + C::TX - 1) / C::TX, DIM == 2 ? (p.ny + C::TY - 1) / C::TY : 1);
-  const size_t b = sizeof(MixSmem<DIM, QP, QC, VAR>);
   switch (stage) {
-    case kStage3: mixed_stage_kernel<DIM, QP, QC, kStage3, VAR><<<grid, C::NT, b, s>>>(p); break;
-    case kStage4: mixed_stage_kernel<DIM, QP, QC, kStage4, VAR><<<grid, C::NT, b, s>>>(p); break;
-    default: mixed_stage_kernel<DIM, QP, QC, kFinal, VAR><<<grid, C::NT, b, s>>>(p); break;
+    case kStage3:
+      mixed_stage_kernel<DIM, QP, QC, kStage3, VAR>
+          <<<grid, C::NT, smem_bytes<DIM, QP, QC, VAR, kStage3>(), s>>>(p);
+      break;
+    case kStage4:
+      mixed_stage_kernel<DIM, QP, QC, kStage4, VAR>
+          <<<grid, C::NT, smem_bytes<DIM, QP, QC, VAR, kStage4>(), s>>>(p);
+      break;
+    default:
+      mixed_stage_kernel<DIM, QP, QC, kFinal, VAR>
+          <<<grid, C::NT, smem_bytes<DIM, QP, QC, VAR, kFinal>(), s>>>(p);
+      break;
   }
   return (int)cudaGetLastError();
 }
@@ -710,11 +756,19 @@ template <int QP, int QC, int VAR>
 int launch_batch_v(const DevParams& p, int stage, cudaStream_t s) {
   using C = TileCfg<1, VAR>;
   const int grid = p.bgrid > 0 ? p.bgrid : 1;
-  const size_t b = sizeof(MixSmem<1, QP, QC, VAR>);
   switch (stage) {
-    case kStage3: mixed_batch_kernel<QP, QC, kStage3, VAR><<<grid, C::NT, b, s>>>(p); break;
-    case kStage4: mixed_batch_kernel<QP, QC, kStage4, VAR><<<grid, C::NT, b, s>>>(p); break;
-    default: mixed_batch_kernel<QP, QC, kFinal, VAR><<<grid, C::NT, b, s>>>(p); break;
+    case kStage3:
+      mixed_batch_kernel<QP, QC, kStage3, VAR>
+          <<<grid, C::NT, smem_bytes<1, QP, QC, VAR, kStage3>(), s>>>(p);
+      break;
+    case kStage4:
+      mixed_batch_kernel<QP, QC, kStage4, VAR>
+          <<<grid, C::NT, smem_bytes<1, QP, QC, VAR, kStage4>(), s>>>(p);
+      break;
+    default:
+      mixed_batch_kernel<QP, QC, kFinal, VAR>
+          <<<grid, C::NT, smem_bytes<1, QP, QC, VAR, kFinal>(), s>>>(p);
+      break;
   }
   return (int)cudaGetLastError();
 }
