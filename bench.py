@@ -71,10 +71,10 @@ BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
 # profiles/stage_kernel_mixed_quadrant512.md, valid for the kernel sources
 # whose SHA-256 (over STAGE_KERNEL_SOURCES in that order, comments removed) is
 # recorded here; reported as null once that code differs.
-TRAFFIC_SRC_SHA256 = "e20554ba54ed01e9ee07376ab1f97caec15456fce8bb4c2af227a364608506a2"
+TRAFFIC_SRC_SHA256 = "0fab2c9867f14de4e0c541e78a5de548b751ae55b0b15be37306729500ac3fe7"
 TRAFFIC_BYTES = {
-    "fp64": {"stage3": 2378509056, "stage4": 2355162624, "final": 1847106560},
-    "mixed": {"stage3": 540218880, "stage4": 673586944, "final": 424611072},
+    "fp64": {"stage3": 2372572672, "stage4": 2354403584, "final": 1841189120},
+    "mixed": {"stage3": 553681664, "stage4": 693669888, "final": 440174848},
 }
 
 
