@@ -102,8 +102,8 @@ def test_named_tableaux(lib):
 
     import numpy as np
 
-    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
-                                       "paper_values.json")))["tableau"]
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")) as fh:
+        gold = json.load(fh)["tableau"]
     imex = fdlb.tableau_dict(fdlb.fdlb_named_tableau(fdlb.FDLB_TABLEAU_IMEX_SSP3_433))
     al, be, et = gold["alpha"], gold["beta"], gold["eta"]
     assert imex["At"] == gold["At"] and imex["wt"] == gold["wt"] and imex["w"] == gold["w"]
