@@ -67,8 +67,7 @@ MIXED_RECORD_BYTES_PER_POP = (24 + 25) * 4 / 128
 BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
                        for k, n in (("stage3", 4), ("stage4", 5), ("final", 3))}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu captures summarised in profiles/stage_kernel_fp64_quadrant512.md and
-# profiles/stage_kernel_mixed_quadrant512.md, valid for the kernel sources
+# ncu captures of the stage kernels on this workload, valid for the kernel sources
 # whose SHA-256 (over STAGE_KERNEL_SOURCES in that order, comments removed) is
 # recorded here; reported as null once that code differs.
 TRAFFIC_SRC_SHA256 = "0fab2c9867f14de4e0c541e78a5de548b751ae55b0b15be37306729500ac3fe7"

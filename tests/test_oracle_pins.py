@@ -365,6 +365,74 @@ def test_advection_derivative_of_polynomial(oracle):
         np.testing.assert_allclose(LF[sl], exact[sl], rtol=1e-9, atol=1e-12)
 
 
+# A non-square 2-D box whose cells are not square: dx = 1.5/24 = 0.0625 and
+# dy = 1.0/40 = 0.025, so any mix-up of the two spacings (or of nx and ny)
+# changes every y-line's flux difference by a factor of 2.5.
+BOX = dict(nx=24, ny=40, x0=0.0, x1=1.5, y0=0.0, y1=1.0)
+
+
+def test_advect_2d_y_lines_use_dy(oracle):
+    """Sec. IV applies the 1-D scheme along each axis with that axis's own
+    spacing.  On the box above, a field that varies only along y has no
+    x-flux (constant lines give F_hat = F_s exactly), and every population's
+    2-D operator equals its 1-D y-line operator with ds = dy, for positive,
+    zero and negative p_y.  The y profile is the cell averages of a monotone
+    degree-8 polynomial, so away from the ghosts the result is also p_y
+    times the polynomial's exact difference quotient over dy."""
+    pr = oracle.Problem(d=2, bc=0, Qphi=5, Qchi=3, gamma=1.4, tau=1e-5, dt=1e-3, **BOX)
+    nx, ny = BOX["nx"], BOX["ny"]
+    dy = (BOX["y1"] - BOX["y0"]) / ny
+    P = np.polyint(np.poly1d(np.poly(np.linspace(-9, -6, 7)))) * 1e-6 + 0.5
+    Pint = np.polyint(P)
+    edges = BOX["y0"] + np.arange(ny + 1) * dy
+    col = (Pint(edges[1:]) - Pint(edges[:-1])) / dy
+    F = np.empty(pr.shape)
+    for k in range(pr.npop):
+        F[k] = (1.0 + 0.1 * k) * col[:, None]
+    LF = oracle.advect(pr, F)
+    p5, _ = oracle.gauss_hermite(5)
+    p3, _ = oracle.gauss_hermite(3)
+    py = [p5[k // 5] for k in range(25)] + [p3[q // 3] for q in range(9)]
+    assert min(py) < 0 < max(py) and 0.0 in py
+    sl = slice(6, ny - 6)
+    for k in range(pr.npop):
+        line = oracle.advect_line(F[k][:, 0].copy(), py[k], dy, bc=0)
+        np.testing.assert_array_equal(LF[k], np.repeat(line[:, None], nx, axis=1))
+        exact = (1.0 + 0.1 * k) * py[k] * (P(edges[1:]) - P(edges[:-1])) / dy
+        np.testing.assert_allclose(LF[k][sl, 0], exact[sl], rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("p_sign", [1, -1])
+def test_linear_advection_2d_mode_along_y(oracle, p_sign):
+    """The 2-D analogue of the Fourier-mode pin above, on the non-square box
+    with periodic ghosts and no collisions: a mode along y of one population
+    with p_x != 0 and p_y of either sign is multiplied in one step by the
+    explicit stability function of (At, wt) at z = -dt |p_y|/dy sigma(theta)
+    (1 - e^{-i theta}) (the x-sweep of an x-constant field is exactly 0)."""
+    ny = BOX["ny"]
+    pr = oracle.Problem(d=2, bc=1, Qphi=3, Qchi=1, gamma=1.4, tau=-1.0, dt=5e-3, **BOX)
+    dy = (BOX["y1"] - BOX["y0"]) / ny
+    theta = 2 * math.pi / 20
+    s = np.arange(ny)
+    c = np.array(golden("paper_values.json")["mp9"]["coefficients_over_2520"]) / 2520.0
+    p, _ = oracle.gauss_hermite(3)
+    At, _, wt, _ = _tab(oracle)
+    k = (2 if p_sign > 0 else 0) * 3 + 2  # ky row of the requested sign, kx = 2 (p_x > 0)
+    F0 = np.ones(pr.shape)
+    F0[k] = (1.0 + 0.01 * np.cos(theta * s))[:, None]
+    F1 = oracle.step(pr, F0, 1)
+    pk = p[k // 3]
+    th = theta if pk > 0 else -theta
+    sigma = np.sum(c * np.exp(1j * th * np.arange(-4, 5)))
+    eig = abs(pk) / dy * sigma * (1 - np.exp(-1j * th))
+    R = _stability(At, wt, -pr.dt * eig)
+    expect = 1.0 + 0.01 * np.real(R * np.exp(1j * theta * s))
+    np.testing.assert_allclose(F1[k], np.repeat(expect[:, None], BOX["nx"], axis=1), rtol=0,
+                               atol=1e-14)
+    others = [j for j in range(pr.npop) if j != k]
+    np.testing.assert_allclose(F1[others], 1.0, rtol=0, atol=1e-15)
+
+
 # --------------------------------------------------------------------------
 # Conservation and symmetries of the full step
 # --------------------------------------------------------------------------
