@@ -132,9 +132,13 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
  * states is a host array of nq*(d+2) doubles; rho > 0 and P > 0 required. */
 int fdlb_init_riemann(fdlb_ctx* ctx, const double* states, int nq, double xsplit, double ysplit);
 
-/* Advance nsteps >= 0 full IMEX steps (all r stages) on the context's stream.
- * Returns FDLB_EUNSTABLE if any cell's moments became invalid during these
- * steps (checked once, after the last step, from a device status word). */
+/* Advance nsteps >= 0 full IMEX steps on the context's stream: each step is
+ * Eq. (IMEX) of Sec. III with the context's tableau (Table I by default), its
+ * r stages each an explicit part R_i with the MP-9 advection of Sec. IV and
+ * an implicit BGK relaxation solved in closed form (Sec. III).  The state is
+ * advanced in place.  Returns FDLB_EUNSTABLE if any cell's moments became
+ * invalid during these steps (checked once, after the last step, from a
+ * device status word); the state then holds the invalid values. */
 int fdlb_step(fdlb_ctx* ctx, int64_t nsteps);
 
 /* fdlb_step that also reports, in stage_ms[0..2], the device time summed over
@@ -148,6 +152,18 @@ int fdlb_step_timed(fdlb_ctx* ctx, int64_t nsteps, double* stage_ms);
  * may be NULL in 1-D), T, each ncells = nx*ny doubles in [ny][nx] order.
  * on_device selects host or device destination pointers. */
 int fdlb_moments(fdlb_ctx* ctx, double* n, double* ux, double* uy, double* T, int on_device);
+
+/* Adjoint of fdlb_moments: the transpose of the Jacobian of (n, ux, uy, T)
+ * with respect to the populations (Eq. Moments_discrete, with
+ * T = (sum phi p^2 + sum chi - n u^2)/((D+K) n)), at the context's current
+ * state.  nbar, uxbar, uybar, Tbar are device arrays of ncells doubles or
+ * NULL (a zero adjoint; uybar is ignored in 1-D); Fbar (device, state layout,
+ * binary64) is overwritten with sum_m mbar_m dm/dF.  The state is read only
+ * when uxbar, uybar or Tbar is given (n is linear in F, so nbar alone needs no
+ * state).  Binary64 single-problem contexts; FDLB_EINVAL otherwise.
+ * Asynchronous on the context's stream. */
+int fdlb_moments_adjoint(fdlb_ctx* ctx, const double* nbar, const double* uxbar,
+                         const double* uybar, const double* Tbar, double* Fbar);
 
 /* Copy the whole state F (layout above) out of / into the context.
  * fdlb_state_bytes gives the size: P * ncells * element size. */
@@ -271,7 +287,9 @@ int fdlb_lattice_nodes(int Q, double* p, double* w);
  * first call before any stream capture.  All calls share the array: two
  * calls whose work overlaps on the GPU (other streams, other threads) race
  * and corrupt each other.  The call synchronises its stream to read the
- * status word; errors are reported through fdlb_last_error(NULL). */
+ * status word; errors are reported through fdlb_last_error(NULL).  When it
+ * returns FDLB_EUNSTABLE, F has already been overwritten and holds the state
+ * in which the invalid moments appeared. */
 int fdlb_step_noalloc(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double tau,
                       double dt, const fdlb_tableau* tableau, double* F, int64_t nsteps,
                       void* cuda_stream);

@@ -40,6 +40,23 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads.  The loops over cells, over (population, line) pairs and over
+ * array elements are shared out with OpenMP; every output element is
+ * computed by one thread with the same operations in the same order as on
+ * one thread, so the results do not depend on the thread count. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------------ */
 /* Sec. II: Gauss-Hermite quadrature                                         */
@@ -315,15 +332,16 @@ int orc_moments(const orc_cfg* c, const double* F, double* n, double* ux, double
   lattice L;
   if (make_lattice(c, &L)) return ORC_EINVAL;
   const long N = (long)c->nx * (c->d == 2 ? c->ny : 1);
-  int rc = ORC_OK;
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(|| : bad)
   for (long i = 0; i < N; ++i) {
     double u[2] = {0.0, 0.0};
     int e = moments_l(&L, F + i, N, &n[i], u, &T[i]);
-    if (e) rc = e;
+    if (e) bad = 1;
     ux[i] = u[0];
     if (uy) uy[i] = u[1];
   }
-  return rc;
+  return bad ? ORC_EUNSTABLE : ORC_OK;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -418,38 +436,47 @@ void orc_advect_line(const double* F, int S, long stride, double p, double ds, i
 
 /* LF = p . grad F for every population (dimensionally unsplit: one 1-D MP-9
  * sweep per axis, the results summed). */
+/* momentum of population k (phi or chi) along axis a */
+static double pop_p(const lattice* L, int k, int a) {
+  if (k < L->nphi) return (a == 1 && L->d == 1) ? 0.0 : phi_p(L, k, a);
+  const int q = k - L->nphi;
+  if (L->d == 1) return a == 0 ? L->pc[q] : 0.0;
+  return a == 0 ? L->pc[q % L->Qc] : L->pc[q / L->Qc];
+}
+
 static void advect_l(const orc_cfg* c, const lattice* Lp, const double* F, double* LF) {
   const lattice L = *Lp;
   const int nx = c->nx, ny = (c->d == 2) ? c->ny : 1;
   const long N = (long)nx * ny;
   const double dx = (c->x1 - c->x0) / nx;
   const double dy = (c->d == 2) ? (c->y1 - c->y0) / ny : 1.0;
-  double* tmp = (double*)malloc(sizeof(double) * (size_t)(nx > ny ? nx : ny));
-  for (int k = 0; k < L.P; ++k) {
-    const double* Fk = F + (long)k * N;
-    double* Lk = LF + (long)k * N;
-    double px, py = 0.0;
-    if (k < L.nphi) {
-      px = phi_p(&L, k, 0);
-      if (L.d == 2) py = phi_p(&L, k, 1);
-    } else {
-      int q = k - L.nphi;
-      px = (L.d == 1) ? L.pc[q] : L.pc[q % L.Qc];
-      if (L.d == 2) py = L.pc[q / L.Qc];
-    }
-    for (long i = 0; i < N; ++i) Lk[i] = 0.0;
-    for (int y = 0; y < ny; ++y) {
-      orc_advect_line(Fk + (long)y * nx, nx, 1, px, dx, c->bc, c->alpha_mp, tmp, 1);
+#pragma omp parallel
+  {
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)(nx > ny ? nx : ny));
+    /* x sweeps: line (k, y) starts row y of population k at 0 and adds its
+     * flux differences */
+#pragma omp for schedule(static)
+    for (long kl = 0; kl < (long)L.P * ny; ++kl) {
+      const int k = (int)(kl / ny), y = (int)(kl % ny);
+      const double* Fk = F + (long)k * N;
+      double* Lk = LF + (long)k * N;
+      for (int x = 0; x < nx; ++x) Lk[(long)y * nx + x] = 0.0;
+      orc_advect_line(Fk + (long)y * nx, nx, 1, pop_p(&L, k, 0), dx, c->bc, c->alpha_mp, tmp, 1);
       for (int x = 0; x < nx; ++x) Lk[(long)y * nx + x] += tmp[x];
     }
+    /* y sweeps (after every x sweep: the loop above ends in a barrier) */
     if (L.d == 2) {
-      for (int x = 0; x < nx; ++x) {
-        orc_advect_line(Fk + x, ny, nx, py, dy, c->bc, c->alpha_mp, tmp, 1);
+#pragma omp for schedule(static)
+      for (long kl = 0; kl < (long)L.P * nx; ++kl) {
+        const int k = (int)(kl / nx), x = (int)(kl % nx);
+        const double* Fk = F + (long)k * N;
+        double* Lk = LF + (long)k * N;
+        orc_advect_line(Fk + x, ny, nx, pop_p(&L, k, 1), dy, c->bc, c->alpha_mp, tmp, 1);
         for (int y = 0; y < ny; ++y) Lk[(long)y * nx + x] += tmp[y];
       }
     }
+    free(tmp);
   }
-  free(tmp);
 }
 
 int orc_advect(const orc_cfg* c, const double* F, double* LF) {
@@ -476,7 +503,11 @@ int orc_init_states(const orc_cfg* c, const double* states, int nq, double xspli
   const double dx = (c->x1 - c->x0) / nx;
   const double dy = (c->d == 2) ? (c->y1 - c->y0) / ny : 0.0;
   if ((c->d == 1 && nq != 2) || (c->d == 2 && nq != 4)) return ORC_EINVAL;
+  int bad = 0;
+#pragma omp parallel reduction(|| : bad)
+  {
   double* feq = (double*)malloc(sizeof(double) * (size_t)L.P);
+#pragma omp for schedule(static)
   for (int y = 0; y < ny; ++y) {
     for (int x = 0; x < nx; ++x) {
       const double xc = c->x0 + (x + 0.5) * dx;
@@ -492,13 +523,14 @@ int orc_init_states(const orc_cfg* c, const double* states, int nq, double xspli
         const double* s = states + 4 * quad;
         rho = s[0]; u[0] = s[1]; u[1] = s[2]; P = s[3];
       }
-      if (!(rho > 0.0) || !(P > 0.0)) { free(feq); return ORC_EINVAL; }
+      if (!(rho > 0.0) || !(P > 0.0)) { bad = 1; continue; }
       equilibrium_l(&L, rho, u, P / rho, feq);
       for (int k = 0; k < L.P; ++k) F[(long)k * N + (long)y * nx + x] = feq[k];
     }
   }
   free(feq);
-  return ORC_OK;
+  }
+  return bad ? ORC_EINVAL : ORC_OK;
 }
 
 /* Arbitrary per-cell (rho, u, T) fields, F = F_eq. */
@@ -507,13 +539,17 @@ int orc_init_fields(const orc_cfg* c, const double* rho, const double* ux, const
   lattice L;
   if (make_lattice(c, &L)) return ORC_EINVAL;
   const long N = (long)c->nx * (c->d == 2 ? c->ny : 1);
-  double* feq = (double*)malloc(sizeof(double) * (size_t)L.P);
-  for (long i = 0; i < N; ++i) {
-    double u[2] = {ux[i], (c->d == 2 && uy) ? uy[i] : 0.0};
-    equilibrium_l(&L, rho[i], u, T[i], feq);
-    for (int k = 0; k < L.P; ++k) F[(long)k * N + i] = feq[k];
+#pragma omp parallel
+  {
+    double* feq = (double*)malloc(sizeof(double) * (size_t)L.P);
+#pragma omp for schedule(static)
+    for (long i = 0; i < N; ++i) {
+      double u[2] = {ux[i], (c->d == 2 && uy) ? uy[i] : 0.0};
+      equilibrium_l(&L, rho[i], u, T[i], feq);
+      for (int k = 0; k < L.P; ++k) F[(long)k * N + i] = feq[k];
+    }
+    free(feq);
   }
-  free(feq);
   return ORC_OK;
 }
 
@@ -547,15 +583,15 @@ int orc_step(const orc_cfg* c, double* F, int nsteps) {
   double* R = (double*)malloc(sizeof(double) * (size_t)PN);
   double* LFs = (double*)calloc((size_t)r * (size_t)PN, sizeof(double));
   double* dFs = (double*)calloc((size_t)r * (size_t)PN, sizeof(double));
-  double* feq = (double*)malloc(sizeof(double) * (size_t)L.P);
-  if (!Fi || !R || !LFs || !dFs || !feq) {
-    free(Fi); free(R); free(LFs); free(dFs); free(feq);
+  if (!Fi || !R || !LFs || !dFs) {
+    free(Fi); free(R); free(LFs); free(dFs);
     return ORC_ENOMEM;
   }
   int rc = ORC_OK;
   for (int step = 0; step < nsteps && rc == ORC_OK; ++step) {
     for (int i = 0; i < r && rc == ORC_OK; ++i) {
       /* explicit part */
+#pragma omp parallel for schedule(static)
       for (long e = 0; e < PN; ++e) {
         double v = F[e];
         for (int j = 0; j < i; ++j) {
@@ -566,33 +602,42 @@ int orc_step(const orc_cfg* c, double* F, int nsteps) {
       }
       /* implicit relaxation, cell by cell */
       const double aii = c->A[i][i];
-      for (long cell = 0; cell < N; ++cell) {
-        double n, u[2] = {0.0, 0.0}, T;
-        int e = moments_l(&L, R + cell, N, &n, u, &T);
-        if (e) { rc = e; break; }
-        equilibrium_l(&L, n, u, T, feq);
-        for (int k = 0; k < L.P; ++k) {
-          const long idx = (long)k * N + cell;
-          const double fi = (R[idx] + aii * lam * feq[k]) / (1.0 + aii * lam);
-          Fi[idx] = fi;
-          dFs[(long)i * PN + idx] = lam * (fi - feq[k]);
+      int bad = 0;
+#pragma omp parallel reduction(|| : bad)
+      {
+        double* fq = (double*)malloc(sizeof(double) * (size_t)L.P);
+#pragma omp for schedule(static)
+        for (long cell = 0; cell < N; ++cell) {
+          double n, u[2] = {0.0, 0.0}, T;
+          if (moments_l(&L, R + cell, N, &n, u, &T)) { bad = 1; continue; }
+          equilibrium_l(&L, n, u, T, fq);
+          for (int k = 0; k < L.P; ++k) {
+            const long idx = (long)k * N + cell;
+            const double fi = (R[idx] + aii * lam * fq[k]) / (1.0 + aii * lam);
+            Fi[idx] = fi;
+            dFs[(long)i * PN + idx] = lam * (fi - fq[k]);
+          }
         }
+        free(fq);
       }
-      if (rc) break;
+      if (bad) { rc = ORC_EUNSTABLE; break; }
       if (need_adv[i]) advect_l(c, &L, Fi, LFs + (long)i * PN);
     }
     if (rc) break;
+    int nonfinite = 0;
+#pragma omp parallel for schedule(static) reduction(|| : nonfinite)
     for (long e = 0; e < PN; ++e) {
       double v = F[e];
       for (int i = 0; i < r; ++i) {
         v -= c->dt * c->wt[i] * LFs[(long)i * PN + e];
         v -= c->w[i] * dFs[(long)i * PN + e];
       }
-      if (!isfinite(v)) rc = ORC_EUNSTABLE;
+      if (!isfinite(v)) nonfinite = 1;
       F[e] = v;
     }
+    if (nonfinite) rc = ORC_EUNSTABLE;
   }
-  free(Fi); free(R); free(LFs); free(dFs); free(feq);
+  free(Fi); free(R); free(LFs); free(dFs);
   return rc;
 }
 

@@ -45,6 +45,9 @@ typedef struct {
 #define ORC_EUNSTABLE -5
 #define ORC_ENOMEM -3
 
+/* Threads of the oracle's loops (OpenMP): n > 0 sets the count, n <= 0
+ * keeps it; returns the count the loops use.  Results do not depend on it. */
+int orc_set_threads(int n);
 int orc_gauss_hermite(int Q, double* p, double* w);
 void orc_he_values(int Q, double x, double* out);
 void orc_g_axis(int Q, const double* p, const double* w, double u, double T, double* g);

@@ -37,8 +37,8 @@ def build(force: bool = False) -> str:
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", _SRC, "-o", tmp, "-lm"]
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+               "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -66,6 +66,7 @@ def _lib_handle():
     with _lock:
         if _lib is None:
             lib = ctypes.CDLL(build())
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_gauss_hermite.argtypes = [ctypes.c_int, _dp, _dp]
             lib.orc_g_axis.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
             lib.orc_g_axis.restype = None
@@ -171,6 +172,12 @@ def paper_tableau() -> dict:
         "wt": [c.wt[i] for i in range(r)],
         "w": [c.w[i] for i in range(r)],
     }
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's OpenMP loops (n > 0 sets, n <= 0 keeps); returns
+    the count in use.  The results are bitwise the same for any count."""
+    return int(_lib_handle().orc_set_threads(int(n)))
 
 
 def gauss_hermite(Q: int):

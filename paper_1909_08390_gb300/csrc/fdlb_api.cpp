@@ -642,6 +642,18 @@ int fdlb_moments(fdlb_ctx* c, double* n, double* ux, double* uy, double* T, int 
   return FDLB_OK;
 }
 
+int fdlb_moments_adjoint(fdlb_ctx* c, const double* nbar, const double* uxbar,
+                         const double* uybar, const double* Tbar, double* Fbar) {
+  if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
+  if (!Fbar) return set_err(c, FDLB_EINVAL, "Fbar is NULL");
+  if (c->batch || c->precision != FDLB_FP64)
+    return set_err(c, FDLB_EINVAL, "fdlb_moments_adjoint: single-problem binary64 contexts");
+  int e = fdlb::launch_moments_adjoint(c->dp, nbar, uxbar, c->dp.d == 2 ? uybar : nullptr, Tbar,
+                                       Fbar, c->stream);
+  if (e) return cuda_err(c, (cudaError_t)e, "moments adjoint kernel launch");
+  return FDLB_OK;
+}
+
 size_t fdlb_state_bytes(const fdlb_ctx* c) {
   if (!c) return 0;
   const size_t esize = c->precision == FDLB_MIXED ? sizeof(float) : sizeof(double);

@@ -104,6 +104,9 @@ int launch_init_riemann(const DevParams& p, const double* states, int nq, double
                         cudaStream_t s);
 int launch_moments(const DevParams& p, double* n, double* ux, double* uy, double* T,
                    cudaStream_t s);
+// J^T of the moment map at the binary64 state p.F (fdlb_moments_adjoint)
+int launch_moments_adjoint(const DevParams& p, const double* nbar, const double* uxbar,
+                           const double* uybar, const double* Tbar, double* Fbar, cudaStream_t s);
 // batch kernels (d = 1, several problems in one launch)
 int launch_batch_stage(const DevParams& p, int stage, cudaStream_t s);
 int launch_batch_init(const DevParams& p, cudaStream_t s);

@@ -335,6 +335,47 @@ __global__ void moments_kernel(const __grid_constant__ DevParams p, double* __re
   T[c] = TT;
 }
 
+// Transpose of the moment map (n, u, T)(F) of Eq. (Moments_discrete) at the
+// current binary64 state: with n = sum phi, u = j/n, j = sum phi p and
+// T = (e - n u^2)/((D+K) n), e = sum phi p^2 + sum chi,
+//   dn/dphi_k = 1,  du_a/dphi_k = (p_a,k - u_a)/n,
+//   dT/dphi_k = (|p_k - u|^2 - (D+K) T)/((D+K) n),  dT/dchi_q = 1/((D+K) n),
+// so Fbar = J^T (nbar, ubar, Tbar) (absent adjoints are zero).  The state is
+// read only when ubar or Tbar is given: n is linear in F.
+template <int DIM, int QP, int QC>
+__global__ void moments_adjoint_kernel(const __grid_constant__ DevParams p,
+                                       const double* __restrict__ nbar,
+                                       const double* __restrict__ uxbar,
+                                       const double* __restrict__ uybar,
+                                       const double* __restrict__ Tbar, double* __restrict__ Fbar) {
+  using L = Lat<DIM, QP, QC>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  const double nb = nbar ? nbar[c] : 0.0;
+  const double uxb = uxbar ? uxbar[c] : 0.0;
+  const double uyb = (DIM == 2 && uybar) ? uybar[c] : 0.0;
+  const double Tb = Tbar ? Tbar[c] : 0.0;
+  double nn = 1.0, vx = 0.0, vy = 0.0, TT = 0.0;
+  if (uxbar || (DIM == 2 && uybar) || Tbar) {
+    Moments m = {};
+    const double* F = (const double*)p.F;
+    for (int pop = 0; pop < L::P; ++pop) accumulate<DIM, QP, QC>(p, m, pop, F[pop * p.N + c]);
+    moments_to_nut<DIM>(p.invDK, m, nn, vx, vy, TT);
+  }
+  const double inv_n = 1.0 / nn;
+  const double tq = Tb * p.invDK * inv_n;  // Tbar / ((D+K) n)
+  for (int pop = 0; pop < L::P; ++pop) {
+    double v;
+    if (pop < L::NPHI) {
+      const double dx = p.px[pop] - vx, dy = DIM == 2 ? p.py[pop] - vy : 0.0;
+      v = nb + (uxb * dx + uyb * dy) * inv_n + tq * (dx * dx + dy * dy - p.DK * TT);
+    } else {
+      v = tq;
+    }
+    Fbar[pop * p.N + c] = v;
+  }
+}
+
 template <int DIM, int QP, int QC, typename S, int VAR>
 int launch_stage_tsv(const DevParams& p, int stage, cudaStream_t s) {
   using C = TileCfg<DIM, VAR>;
@@ -468,6 +509,20 @@ int launch_moments(const DevParams& p, double* n, double* ux, double* uy, double
                    cudaStream_t s) {
 #define X(D_, P_, C_) \
   if (p.d == D_ && p.Qp == P_ && p.Qc == C_) return launch_moments_t<D_, P_, C_>(p, n, ux, uy, T, s);
+  FDLB_LATTICES(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_moments_adjoint(const DevParams& p, const double* nbar, const double* uxbar,
+                           const double* uybar, const double* Tbar, double* Fbar, cudaStream_t s) {
+  const int nt = 128;
+  const unsigned nb = (unsigned)((p.N + nt - 1) / nt);
+#define X(D_, P_, C_)                                                                       \
+  if (p.d == D_ && p.Qp == P_ && p.Qc == C_) {                                              \
+    moments_adjoint_kernel<D_, P_, C_><<<nb, nt, 0, s>>>(p, nbar, uxbar, uybar, Tbar, Fbar); \
+    return (int)cudaGetLastError();                                                         \
+  }
   FDLB_LATTICES(X)
 #undef X
   return (int)cudaErrorInvalidValue;

@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fdlb_step.argtypes = [_vp, ctypes.c_int64]
     lib.fdlb_step_timed.argtypes = [_vp, ctypes.c_int64, _dp]
     lib.fdlb_moments.argtypes = [_vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+    lib.fdlb_moments_adjoint.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp]
     lib.fdlb_state_bytes.argtypes = [_vp]
     lib.fdlb_state_bytes.restype = ctypes.c_size_t
     lib.fdlb_get_state.argtypes = [_vp, _vp, ctypes.c_int]
@@ -175,6 +176,14 @@ def fdlb_step_timed(ctx, nsteps: int):
 def fdlb_moments(ctx, n, ux, uy, T, on_device: bool):
     ptr = (lambda a: None if a is None else (a.data_ptr() if on_device else a.ctypes.data))
     _check(load().fdlb_moments(ctx, ptr(n), ptr(ux), ptr(uy), ptr(T), int(on_device)), ctx)
+
+
+def fdlb_moments_adjoint(ctx, nbar, uxbar, uybar, Tbar, Fbar):
+    """Fbar = J^T (nbar, uxbar, uybar, Tbar) at the context's state (device
+    float64 tensors; None for a zero adjoint)."""
+    ptr = (lambda a: None if a is None else a.data_ptr())
+    _check(load().fdlb_moments_adjoint(ctx, ptr(nbar), ptr(uxbar), ptr(uybar), ptr(Tbar),
+                                       Fbar.data_ptr()), ctx)
 
 
 def fdlb_state_bytes(ctx) -> int:
@@ -464,19 +473,26 @@ def _field_context(spec, gamma: float, tau: float, n0, u0, T0):
     return ctx, Qphi
 
 
+def _density(ctx, nx: int, device):
+    """The density of the context's state, from the library's moments kernel."""
+    import torch
+    n, u, T = (torch.empty(nx, dtype=torch.float64, device=device) for _ in range(3))
+    fdlb_moments(ctx, n, u, None, T, True)
+    return n
+
+
 def density_forward(n0, u0, T0, gamma, tau, spec):
     """Final density after spec['nsteps'] steps from the equilibrium of the
     fields (no gradient; the plain fdlb_step path)."""
     import torch
-    ctx, Qphi = _field_context(spec, gamma, tau, n0, u0, T0)
+    ctx, _ = _field_context(spec, gamma, tau, n0, u0, T0)
     try:
         fdlb_step(ctx, spec["nsteps"])
-        FN = torch.empty((fdlb_npop(ctx), spec["nx"]), dtype=torch.float64, device=n0.device)
-        fdlb_get_state(ctx, FN, True)
+        n = _density(ctx, spec["nx"], n0.device)
         torch.cuda.current_stream().synchronize()
     finally:
         fdlb_destroy(ctx)
-    return FN[:Qphi].sum(0)
+    return n
 
 
 def _autograd_function():
@@ -499,24 +515,27 @@ def _autograd_function():
                 ckpt = torch.empty((nsteps // every + 1, P, spec["nx"]), dtype=torch.float64,
                                    device=n0.device)
                 fdlb_forward_ckpt(ctx, nsteps, every, ckpt)
-                FN = torch.empty((P, spec["nx"]), dtype=torch.float64, device=n0.device)
-                fdlb_get_state(ctx, FN, True)
+                n = _density(ctx, spec["nx"], n0.device)
                 torch.cuda.current_stream().synchronize()
             finally:
                 fdlb_destroy(ctx)
-            fctx.ckpt, fctx.spec, fctx.Qphi, fctx.P = ckpt, spec, Qphi, P
+            fctx.ckpt, fctx.spec, fctx.P = ckpt, spec, P
             fctx.gamma, fctx.tau = float(gamma), float(tau)
             fctx.save_for_backward(*(t.detach().to(torch.float64).contiguous() for t in (n0, u0, T0)))
-            return FN[:Qphi].sum(0)  # n = sum of the phi populations (Eq. Moments_discrete)
+            return n
 
         @staticmethod
         def backward(fctx, nbar):
             n0, u0, T0 = fctx.saved_tensors
             spec = fctx.spec
-            Fbar = torch.zeros((fctx.P, spec["nx"]), dtype=torch.float64, device=nbar.device)
-            Fbar[:fctx.Qphi] = nbar.to(torch.float64)
+            Fbar = torch.empty((fctx.P, spec["nx"]), dtype=torch.float64, device=nbar.device)
             ctx, _ = _field_context(spec, fctx.gamma, fctx.tau, n0, u0, T0)
             try:
+                # dLoss/dF(nsteps) from dLoss/dn: the library's transpose of
+                # the moment map (n is linear in F, so the context's current
+                # state does not enter)
+                fdlb_moments_adjoint(ctx, nbar.to(torch.float64).contiguous(), None, None, None,
+                                     Fbar)
                 dg, dtau = fdlb_adjoint(ctx, spec["nsteps"], spec["every"], fctx.ckpt, Fbar)
                 nb, ub, Tb = (torch.empty_like(n0) for _ in range(3))
                 dg0 = fdlb_init_fields_adjoint(ctx, Fbar, n0, u0, T0, nb, ub, Tb)

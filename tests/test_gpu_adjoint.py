@@ -113,6 +113,50 @@ def test_dot_product_state(F, torch, Q, nx, nsteps):
         F.fdlb_destroy(ctx)
 
 
+@pytest.mark.parametrize("d,Q,nx", [(1, (8, 8), 300), (1, (5, 3), 77), (2, (8, 8), 37),
+                                    (2, (5, 3), 29)])
+def test_moments_adjoint_dot_product(F, torch, d, Q, nx):
+    """fdlb_moments_adjoint is the transpose of the moment map (n, u, T)(F) of
+    Eq. (Moments_discrete): <mbar, J dF> by central differences of
+    fdlb_moments equals <J^T mbar, dF>; with nbar alone it is nbar on every
+    phi population and 0 on every chi population (n = sum phi)."""
+    ctx = make_ctx(F, nx, Q, d=d)
+    try:
+        P = F.fdlb_npop(ctx)
+        shape = (P, nx) if d == 1 else (P, nx, nx)
+        S0 = torch.as_tensor(W.smooth_random_populations(shape, seed=9, amp=0.2), device="cuda")
+        dF = torch.as_tensor(W.smooth_random_populations(shape, seed=10, amp=1.0) - 1.0,
+                             device="cuda") * S0
+        g = torch.Generator(device="cpu").manual_seed(3)
+        cells = shape[1:]
+        mbar = [torch.randn(cells, generator=g, dtype=torch.float64).cuda() for _ in range(4)]
+        if d == 1:
+            mbar[2] = None
+
+        def moments(S):
+            F.fdlb_set_state(ctx, S.contiguous(), True)
+            out = [torch.empty(cells, dtype=torch.float64, device="cuda") for _ in range(4)]
+            F.fdlb_moments(ctx, out[0], out[1], out[2] if d == 2 else None, out[3], True)
+            torch.cuda.synchronize()
+            return out
+
+        h = 1e-6
+        mp, mm = moments(S0 + h * dF), moments(S0 - h * dF)
+        lhs = sum(float((b * (x - y)).sum()) for b, x, y in zip(mbar, mp, mm) if b is not None)
+        lhs /= 2 * h
+        F.fdlb_set_state(ctx, S0.contiguous(), True)
+        Fb = torch.empty(shape, dtype=torch.float64, device="cuda")
+        F.fdlb_moments_adjoint(ctx, *mbar, Fb)
+        rhs = float((Fb * dF).sum())
+        assert abs(lhs - rhs) <= 1e-8 * abs(rhs), (lhs, rhs)
+        F.fdlb_moments_adjoint(ctx, mbar[0], None, None, None, Fb)
+        nphi = Q[0] ** d
+        torch.testing.assert_close(Fb[:nphi], mbar[0].expand_as(Fb[:nphi]), rtol=0, atol=0)
+        assert float(Fb[nphi:].abs().max()) == 0.0
+    finally:
+        F.fdlb_destroy(ctx)
+
+
 @pytest.mark.parametrize("which", ["gamma", "tau"])
 def test_parameter_derivatives_of_steps(F, torch, which):
     """dparams of fdlb_adjoint against central differences of the steps in
