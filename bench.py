@@ -58,14 +58,16 @@ FP64_OPS_PER_POP = {"stage3": 30 + 4 + 13, "stage4": 30 + 4 + 11, "final": 30 + 
 # written once each by the kernel (stage 3: F2, F, D -> F3, A4, Af, D3;
 # stage 4: F3, A4, Af, D3 -> F4, Af, D4; final: F4, Af, D4 -> F, D, F2).
 BYTES_PER_POP = {"stage3": 7 * 8, "stage4": 7 * 8, "final": 6 * 8}
-# Mixed precision (single-pass kernels, 4 B per population): stage 3 reads
-# F^n and writes R3, A4', Af'; stage 4 reads R3, A4', Af' and writes R4, Af'';
-# the final stage reads R4, Af'' and writes F^{n+1}; plus, per cell, the
-# equilibrium record's components read (24: A, B and C B) and written (25, C
-# too) for the 8x8 lattice: (24 + 25) * 4 / 128 B per population.
-MIXED_RECORD_BYTES_PER_POP = (24 + 25) * 4 / 128
-BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_RECORD_BYTES_PER_POP
-                       for k, n in (("stage3", 4), ("stage4", 5), ("final", 3))}
+# Mixed precision (single-pass kernels; binary32 arrays, 4 B per population
+# and array): stage 3 reads sh, sl and writes r3l, a4l, afl; stage 4 reads
+# sh, r3l, a4l, afl and writes a4l, afl; the final stage reads sh, a4l, afl and
+# writes the next state's nh, nl.  Per cell and kernel, for the 8x8 lattice:
+# the equilibrium record read (24 binary32-pair components: A, B and C B) and
+# written (25, C too), and the binary64 moment sums of sh (4 doubles) read by
+# stages 3 and 4 and written by the final stage.
+MIXED_CELL_BYTES_PER_POP = ((24 + 25) * 8 + 4 * 8) / 128
+BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_CELL_BYTES_PER_POP
+                       for k, n in (("stage3", 5), ("stage4", 6), ("final", 5))}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # ncu captures of the stage kernels on this workload, valid for the kernel sources
 # whose SHA-256 (over STAGE_KERNEL_SOURCES in that order, comments removed) is
@@ -440,12 +442,18 @@ def run_ours(args, world, rank, local):
     achieved_gops = ops / (per_launch_ms * 1e-3) / 1e9
     hbm_bytes = BYTES_PER_POP[names[top]] * units_per_step
     peaks = _load_peaks()
+    # the binary64 pipe's measured ceiling: independent DFMA chains on every SM
+    # (fdlb_measure_fp64_pipe), taken after the timed region
+    dfma_rate, _ = fdlb.fdlb_measure_fp64_pipe(stream)
+    meas_gops = dfma_rate / 1e9
     roofline = {
         "bound": "alu", "kernel": f"stage_kernel<2,8,8,{names[top]}>",
-        "achieved": achieved_gops, "peak": FP64_PEAK_GOPS, "unit": "G binary64 op/s",
-        "frac": achieved_gops / FP64_PEAK_GOPS,
-        "peak_source": "binary64 pipe, nominal: 152 SMs x 2 lanes/clk x 2.07 GHz (1.26 TFLOP/s "
-                       "with FMA = 2); MEASURED_PEAKS.json has no binary64 figure",
+        "achieved": achieved_gops, "peak": meas_gops, "unit": "G binary64 op/s",
+        "frac": achieved_gops / meas_gops,
+        "peak_source": "measured: fdlb_measure_fp64_pipe, 8 independent DFMA chains per thread, "
+                       "2048 threads per SM (MEASURED_PEAKS.json has no binary64 figure)",
+        "peak_nominal": FP64_PEAK_GOPS, "frac_of_nominal": achieved_gops / FP64_PEAK_GOPS,
+        "peak_nominal_source": "152 SMs x 2 binary64 lanes/clk x 2.07 GHz",
         "traffic": _traffic("fp64", names[top]),
         "algorithmic_ops_per_launch": ops,
         "achieved_tflops": achieved_tflops, "tflops_frac": achieved_tflops / FP64_PEAK_TFLOPS,
@@ -526,7 +534,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         b_ms = _max_over_ranks(world, b0.elapsed_time(b1))
         b_units = bs.P * total_cells * args.steps  # all ranks' problems
-        b_gbs = ((48 + 3 * 2 * 9 * 4 / 16) * bs.P * total_cells / world
+        b_gbs = ((64 + 3 * (2 * 9 * 8 + 4 * 8) / 16) * bs.P * total_cells / world
                  / (b_ms / args.steps * 1e-3) / 1e9)
         flags = bs.status()
         bs.close()
@@ -567,8 +575,9 @@ def run_ours(args, world, rank, local):
             "tiling": {"cells_per_tile": [127, 63, 255][variant], "ctas_per_sm": ctas},
             "unstable_members": int(_sum_over_ranks(world, float((flags != 0).sum()))),
             # whole-step algorithmic HBM bytes of the three single-pass kernels:
-            # 12 population arrays of 4 B and, per kernel, one 9-component cell
-            # record read and one written (2 * 9 * 4 / 16 B per population)
+            # 16 population-array accesses of 4 B and, per kernel and cell, one
+            # 9-component record of binary32 pairs read and one written and the
+            # 4 binary64 moment sums ((2 * 9 * 8 + 32) / 16 B per population)
             "roofline": {
                 "bound": "hbm", "scope": "whole step (3 kernels), per GPU",
                 "achieved": b_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",

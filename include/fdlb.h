@@ -294,6 +294,16 @@ int fdlb_step_noalloc(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, d
                       double dt, const fdlb_tableau* tableau, double* F, int64_t nsteps,
                       void* cuda_stream);
 
+/* Measurement aid (no paper counterpart): the sustained binary64 fused
+ * multiply-add rate of the current device, in DFMA per second, from a kernel
+ * of 8 independent DFMA chains per thread on 8 CTAs of 256 threads per SM
+ * (best of three timed launches after one warm-up, CUDA events on
+ * cuda_stream).  This is the measured ceiling of the binary64 pipe that
+ * bounds the binary64 stage kernels; an add or a multiply takes the same pipe
+ * slot as an FMA.  *ms_out (may be NULL) receives the timed launch's ms.
+ * Synchronises the stream; FDLB_ECUDA on a CUDA failure. */
+int fdlb_measure_fp64_pipe(void* cuda_stream, double* dfma_per_s, double* ms_out);
+
 /* Release the context and its device buffers (NULL is a no-op). */
 void fdlb_destroy(fdlb_ctx* ctx);
 

@@ -20,10 +20,12 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfdlb.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-SOURCES = ["fdlb_kernels.cu", "fdlb_mixed.cu", "fdlb_api.cpp", "fdlb_noalloc.cu", "fdlb_adjoint.cu"]
+SOURCES = ["fdlb_kernels.cu", "fdlb_mixed.cu", "fdlb_api.cpp", "fdlb_noalloc.cu", "fdlb_adjoint.cu",
+           "fdlb_peak.cu"]
 HEADERS = [os.path.join(CSRC, "fdlb_internal.h"), os.path.join(CSRC, "fdlb_ctx.h"),
            os.path.join(CSRC, "fdlb_device.cuh"),
-           os.path.join(CSRC, "fdlb_mp9.cuh"), os.path.join(INCLUDE, "fdlb.h")]
+           os.path.join(CSRC, "fdlb_mp9.cuh"), os.path.join(CSRC, "fdlb_tile.cuh"),
+           os.path.join(INCLUDE, "fdlb.h")]
 
 
 def _cuda_home() -> str:

@@ -211,17 +211,42 @@ int launch_stage_any(const fdlb_ctx* c, int stage, cudaStream_t s) {
   return c->batch ? fdlb::launch_batch_stage(c->dp, stage, s) : fdlb::launch_stage(c->dp, stage, s);
 }
 
-constexpr int kGraphSteps = 16;  // steps per captured graph
+constexpr int kGraphSteps = 16;  // steps per captured graph (even: see step_launch)
 
-void drop_graph(fdlb_ctx* c) {
-  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-  c->graph_exec = nullptr;
+// Point the stage kernels of a FDLB_MIXED context at the current state buffer
+// (pair[parity]) and the one the final stage writes.
+void set_pair_pointers(fdlb_ctx* c) {
+  if (c->precision != FDLB_MIXED) return;
+  c->dp.sh = c->pair[c->parity][0];
+  c->dp.sl = c->pair[c->parity][1];
+  c->dp.nh = c->pair[1 - c->parity][0];
+  c->dp.nl = c->pair[1 - c->parity][1];
 }
 
-// Capture kGraphSteps steps (3 kernels each) on a private stream once; the
-// graph then replays on the context's stream.
+// One stage kernel of a step; after the final stage of a FDLB_MIXED context
+// the new state is in the other buffer, which becomes the current one.
+int step_launch(fdlb_ctx* c, int stage, cudaStream_t s) {
+  const int e = launch_stage_any(c, stage, s);
+  if (!e && stage == fdlb::kFinal && c->precision == FDLB_MIXED) {
+    c->parity ^= 1;
+    set_pair_pointers(c);
+  }
+  return e;
+}
+
+void drop_graph(fdlb_ctx* c) {
+  for (auto& g : c->graph_exec) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
+}
+
+// Capture kGraphSteps steps (3 kernels each) on a private stream once per
+// starting state buffer; the graph then replays on the context's stream.
+// kGraphSteps is even, so a replay ends in the buffer it started from.
 int ensure_graph(fdlb_ctx* c) {
-  if (c->graph_exec) return FDLB_OK;
+  if (c->graph_exec[c->parity]) return FDLB_OK;
+  const int start_parity = c->parity;
   cudaError_t e = cudaSuccess;
   if (!c->capture_stream) e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_err(c, e, "capture stream");
@@ -230,7 +255,10 @@ int ensure_graph(fdlb_ctx* c) {
   int le = 0;
   for (int k = 0; k < kGraphSteps && !le; ++k)
     for (int st : {fdlb::kStage3, fdlb::kStage4, fdlb::kFinal})
-      if (!le) le = launch_stage_any(c, st, c->capture_stream);
+      if (!le) le = step_launch(c, st, c->capture_stream);
+  // the capture ran nothing: the state is where it was
+  c->parity = start_parity;
+  set_pair_pointers(c);
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(c->capture_stream, &g);
   if (le) {
@@ -238,14 +266,67 @@ int ensure_graph(fdlb_ctx* c) {
     return cuda_err(c, (cudaError_t)le, "kernel launch during capture");
   }
   if (e != cudaSuccess) return cuda_err(c, e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+  e = cudaGraphInstantiate(&c->graph_exec[start_parity], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    c->graph_exec = nullptr;
+    c->graph_exec[start_parity] = nullptr;
     return cuda_err(c, e, "cudaGraphInstantiate");
   }
   return FDLB_OK;
 }
+
+// Device buffers of a context: FDLB_FP64, six binary64 population arrays
+// (F, F2, F3, A4, A_fin, D); FDLB_MIXED, seven binary32 population arrays
+// (the two state buffers hi and lo, r3l, a4l, afl) and the per-cell mhi;
+// then the four moment fields for host copies, the status word, and the
+// FDLB_MIXED records (three of 2 recw binary32 components per cell).
+struct Layout {
+  size_t arr, mom, mhi, rec, total;
+};
+
+Layout buffer_layout(int precision, int P, int64_t N, int recw) {
+  Layout L{};
+  const size_t esize = precision == FDLB_MIXED ? sizeof(float) : sizeof(double);
+  L.arr = ((size_t)P * (size_t)N * esize + 255) / 256 * 256;
+  const size_t narr = precision == FDLB_MIXED ? 7 : 6;
+  L.mom = narr * L.arr;
+  L.mhi = L.mom + 4 * (size_t)N * sizeof(double) + 256;
+  L.rec = L.mhi + (precision == FDLB_MIXED ? 4 * (size_t)N * sizeof(double) : 0);
+  const size_t rec_one = (2 * (size_t)recw * (size_t)N * sizeof(float) + 255) / 256 * 256;
+  L.total = L.rec + 3 * rec_one;
+  return L;
+}
+
+// Assign the buffer pointers of c->dp from the layout (c->buf allocated).
+void assign_buffers(fdlb_ctx* c, const Layout& L) {
+  fdlb::DevParams& p = c->dp;
+  char* b = (char*)c->buf;
+  if (c->precision == FDLB_MIXED) {
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) c->pair[i][j] = (float*)(b + (2 * i + j) * L.arr);
+    p.r3l = (float*)(b + 4 * L.arr);
+    p.a4l = (float*)(b + 5 * L.arr);
+    p.afl = (float*)(b + 6 * L.arr);
+    p.mhi = (double*)(b + L.mhi);
+    c->parity = 0;
+    set_pair_pointers(c);
+  } else {
+    p.F = b + 0 * L.arr;
+    p.F2 = b + 1 * L.arr;
+    p.F3 = b + 2 * L.arr;
+    p.A4 = b + 3 * L.arr;
+    p.Af = b + 4 * L.arr;
+    p.D = b + 5 * L.arr;
+  }
+  c->mom = (double*)(b + L.mom);
+  p.status = (unsigned*)(b + L.mom + 4 * (size_t)p.N * sizeof(double));
+  const size_t rec_one = (2 * (size_t)p.recw * (size_t)p.N * sizeof(float) + 255) / 256 * 256;
+  for (int i = 0; i < 3; ++i) p.erec[i] = p.recw ? (float*)(b + L.rec + i * rec_one) : nullptr;
+}
+
+// A binary64 scratch array of P * N values for moving a FDLB_MIXED state to
+// or from the host: r3l and a4l, which hold nothing between steps.
+double* mixed_exchange_buffer(fdlb_ctx* c) { return (double*)c->dp.r3l; }
 
 int ensure_prepared(fdlb_ctx* c) {
   if (c->prepared) return FDLB_OK;
@@ -488,13 +569,10 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
     return cuda_err(nullptr, e, "cudaGetDevice");
   }
   p.precision = precision;
-  const size_t esize = precision == FDLB_MIXED ? sizeof(float) : sizeof(double);
-  const size_t arr = (size_t)p.P * (size_t)N * esize;
-  const size_t mom_bytes = 4 * (size_t)N * sizeof(double);
   // binary32 contexts: three per-cell equilibrium records (fdlb_mixed.cu)
   p.recw = precision == FDLB_MIXED ? fdlb::mixed_record_width(g.d, Qphi, Qchi) : 0;
-  const size_t rec_bytes = ((size_t)p.recw * (size_t)N * sizeof(float) + 255) / 256 * 256;
-  c->buf_bytes = 6 * arr + mom_bytes + 256 + 3 * rec_bytes;
+  const Layout lay = buffer_layout(precision, p.P, N, p.recw);
+  c->buf_bytes = lay.total;
   e = cudaMalloc(&c->buf, c->buf_bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -503,17 +581,7 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
     return set_err(nullptr, FDLB_ENOMEM, "cudaMalloc(%zu) failed: %s", want,
                    cudaGetErrorString(e));
   }
-  char* b = (char*)c->buf;
-  p.F = b + 0 * arr;
-  p.F2 = b + 1 * arr;
-  p.F3 = b + 2 * arr;
-  p.A4 = b + 3 * arr;
-  p.Af = b + 4 * arr;
-  p.D = b + 5 * arr;
-  c->mom = (double*)(b + 6 * arr);
-  p.status = (unsigned*)(b + 6 * arr + mom_bytes);
-  for (int i = 0; i < 3; ++i)
-    p.erec[i] = p.recw ? (float*)(b + 6 * arr + mom_bytes + 256 + i * rec_bytes) : nullptr;
+  assign_buffers(c, lay);
   e = cudaMallocHost(&c->status_host, sizeof(unsigned));
   if (e == cudaSuccess && precision == FDLB_MIXED) e = (cudaError_t)fdlb::mixed_setup(p);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->buf, 0, c->buf_bytes, c->stream);
@@ -561,13 +629,13 @@ int fdlb_step(fdlb_ctx* c, int64_t nsteps) {
     rc = ensure_graph(c);
     if (rc) return rc;
     for (; left >= kGraphSteps; left -= kGraphSteps) {
-      cudaError_t ge = cudaGraphLaunch(c->graph_exec, c->stream);
+      cudaError_t ge = cudaGraphLaunch(c->graph_exec[c->parity], c->stream);
       if (ge != cudaSuccess) return cuda_err(c, ge, "cudaGraphLaunch");
     }
   }
   for (int64_t s = 0; s < left; ++s) {
     for (int st : {fdlb::kStage3, fdlb::kStage4, fdlb::kFinal}) {
-      int e = launch_stage_any(c, st, c->stream);
+      int e = step_launch(c, st, c->stream);
       if (e) return cuda_err(c, (cudaError_t)e, "stage kernel launch");
     }
   }
@@ -594,7 +662,7 @@ int fdlb_step_timed(fdlb_ctx* c, int64_t nsteps, double* stage_ms) {
   if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
   for (int64_t s = 0; s < nsteps && e == cudaSuccess; ++s) {
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-      int le = launch_stage_any(c, kinds[k], c->stream);
+      int le = step_launch(c, kinds[k], c->stream);
       if (le) e = (cudaError_t)le;
       if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + k + 1], c->stream);
     }
@@ -656,16 +724,25 @@ int fdlb_moments_adjoint(fdlb_ctx* c, const double* nbar, const double* uxbar,
 
 size_t fdlb_state_bytes(const fdlb_ctx* c) {
   if (!c) return 0;
-  const size_t esize = c->precision == FDLB_MIXED ? sizeof(float) : sizeof(double);
-  return (size_t)c->dp.P * (size_t)c->dp.N * esize;
+  return (size_t)c->dp.P * (size_t)c->dp.N * sizeof(double);
 }
 
 int fdlb_get_state(fdlb_ctx* c, void* dst, int on_device) {
   if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
   if (!dst) return set_err(c, FDLB_EINVAL, "dst is NULL");
-  cudaError_t e = cudaMemcpyAsync(dst, c->dp.F, fdlb_state_bytes(c),
-                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                  c->stream);
+  cudaError_t e = cudaSuccess;
+  if (c->precision == FDLB_MIXED) {
+    // the exact binary64 value hi + lo of every population
+    double* dev = on_device ? (double*)dst : mixed_exchange_buffer(c);
+    const int64_t n = (int64_t)c->dp.P * c->dp.N;
+    int le = fdlb::launch_pair_to_double(c->dp.sh, c->dp.sl, dev, n, c->stream);
+    if (le) e = (cudaError_t)le;
+    if (e == cudaSuccess && !on_device)
+      e = cudaMemcpyAsync(dst, dev, fdlb_state_bytes(c), cudaMemcpyDeviceToHost, c->stream);
+  } else {
+    e = cudaMemcpyAsync(dst, c->dp.F, fdlb_state_bytes(c),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+  }
   if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_err(c, e, "fdlb_get_state");
   return FDLB_OK;
@@ -674,9 +751,24 @@ int fdlb_get_state(fdlb_ctx* c, void* dst, int on_device) {
 int fdlb_set_state(fdlb_ctx* c, const void* src, int on_device) {
   if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
   if (!src) return set_err(c, FDLB_EINVAL, "src is NULL");
-  cudaError_t e = cudaMemcpyAsync(c->dp.F, src, fdlb_state_bytes(c),
-                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                  c->stream);
+  cudaError_t e = cudaSuccess;
+  if (c->precision == FDLB_MIXED) {
+    // each binary64 value v becomes hi = v rounded, lo = (v - hi) rounded
+    const double* dev = (const double*)src;
+    if (!on_device) {
+      e = cudaMemcpyAsync(mixed_exchange_buffer(c), src, fdlb_state_bytes(c),
+                          cudaMemcpyHostToDevice, c->stream);
+      dev = mixed_exchange_buffer(c);
+    }
+    const int64_t n = (int64_t)c->dp.P * c->dp.N;
+    if (e == cudaSuccess) {
+      int le = fdlb::launch_double_to_pair(dev, c->dp.sh, c->dp.sl, n, c->stream);
+      if (le) e = (cudaError_t)le;
+    }
+  } else {
+    e = cudaMemcpyAsync(c->dp.F, src, fdlb_state_bytes(c),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  }
   if (e != cudaSuccess) return cuda_err(c, e, "fdlb_set_state");
   c->prepared = false;
   int rc = ensure_prepared(c);
@@ -790,13 +882,10 @@ int fdlb_create_batch(int nprob, const int64_t* nx, const double* gamma, double 
     return cuda_err(nullptr, e, "device query");
   }
   p.bgrid = 4 * c->nsm;
-  const size_t esize = precision == FDLB_MIXED ? sizeof(float) : sizeof(double);
-  const size_t arr = (size_t)p.P * (size_t)total * esize;
-  const size_t mom_bytes = 4 * (size_t)total * sizeof(double);
   const size_t pstat_bytes = ((size_t)nprob * sizeof(unsigned) + 255) / 256 * 256;
   p.recw = precision == FDLB_MIXED ? fdlb::mixed_record_width(1, Qphi, Qchi) : 0;
-  const size_t rec_bytes = ((size_t)p.recw * (size_t)total * sizeof(float) + 255) / 256 * 256;
-  c->buf_bytes = 6 * arr + mom_bytes + 256 + pstat_bytes + 3 * rec_bytes;
+  const Layout lay = buffer_layout(precision, p.P, total, p.recw);
+  c->buf_bytes = lay.total + pstat_bytes;
   e = cudaMalloc(&c->buf, c->buf_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->probs_dev, nprob * sizeof(fdlb::BatchProblem));
   if (e != cudaSuccess) {
@@ -804,19 +893,8 @@ int fdlb_create_batch(int nprob, const int64_t* nx, const double* gamma, double 
     fdlb_destroy(c);
     return set_err(nullptr, FDLB_ENOMEM, "batch allocation failed: %s", cudaGetErrorString(e));
   }
-  char* b = (char*)c->buf;
-  p.F = b + 0 * arr;
-  p.F2 = b + 1 * arr;
-  p.F3 = b + 2 * arr;
-  p.A4 = b + 3 * arr;
-  p.Af = b + 4 * arr;
-  p.D = b + 5 * arr;
-  c->mom = (double*)(b + 6 * arr);
-  p.status = (unsigned*)(b + 6 * arr + mom_bytes);
-  p.pstatus = (unsigned*)(b + 6 * arr + mom_bytes + 256);
-  for (int i = 0; i < 3; ++i)
-    p.erec[i] = p.recw ? (float*)(b + 6 * arr + mom_bytes + 256 + pstat_bytes + i * rec_bytes)
-                       : nullptr;
+  assign_buffers(c, lay);
+  p.pstatus = (unsigned*)((char*)c->buf + lay.total);
   p.probs = c->probs_dev;
   e = cudaMallocHost(&c->status_host, sizeof(unsigned));
   if (e == cudaSuccess && precision == FDLB_MIXED) e = (cudaError_t)fdlb::mixed_setup(p);
@@ -878,12 +956,23 @@ int fdlb_autotune(fdlb_ctx* c, int trial_steps, int* variant_out, int* ctas_per_
   if (trial_steps < 1) trial_steps = 2;
   int rc = ensure_prepared(c);
   if (rc) return rc;
-  // keep the state: every trial starts from it
+  // keep the state (as binary64 values): every trial starts from it
   const size_t bytes = fdlb_state_bytes(c);
   void* saved = nullptr;
   cudaError_t e = cudaMalloc(&saved, bytes);
   if (e != cudaSuccess) return set_err(c, FDLB_ENOMEM, "autotune buffer: %s", cudaGetErrorString(e));
-  e = cudaMemcpyAsync(saved, c->dp.F, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  auto put_state = [&](bool restore) -> cudaError_t {
+    if (c->precision == FDLB_MIXED) {
+      const int64_t n = (int64_t)c->dp.P * c->dp.N;
+      return (cudaError_t)(restore ? fdlb::launch_double_to_pair((const double*)saved, c->dp.sh,
+                                                                 c->dp.sl, n, c->stream)
+                                   : fdlb::launch_pair_to_double(c->dp.sh, c->dp.sl,
+                                                                 (double*)saved, n, c->stream));
+    }
+    return restore ? cudaMemcpyAsync(c->dp.F, saved, bytes, cudaMemcpyDeviceToDevice, c->stream)
+                   : cudaMemcpyAsync(saved, c->dp.F, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  };
+  e = put_state(false);
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&t0);
   if (e == cudaSuccess) e = cudaEventCreate(&t1);
@@ -895,12 +984,12 @@ int fdlb_autotune(fdlb_ctx* c, int trial_steps, int* variant_out, int* ctas_per_
     if ((rc = upload_work(c))) break;
     for (int k : ctas) {
       c->dp.bgrid = k * c->nsm;
-      e = cudaMemcpyAsync(c->dp.F, saved, bytes, cudaMemcpyDeviceToDevice, c->stream);
+      e = put_state(true);
       int le = e == cudaSuccess ? launch_stage_any(c, fdlb::kPrep, c->stream) : 0;
       if (e == cudaSuccess) e = cudaEventRecord(t0, c->stream);
       for (int s = 0; s < trial_steps && e == cudaSuccess && !le; ++s)
         for (int st : {fdlb::kStage3, fdlb::kStage4, fdlb::kFinal})
-          if (!le) le = launch_stage_any(c, st, c->stream);
+          if (!le) le = step_launch(c, st, c->stream);
       if (le) e = (cudaError_t)le;
       if (e == cudaSuccess) e = cudaEventRecord(t1, c->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(t1);
@@ -918,7 +1007,7 @@ int fdlb_autotune(fdlb_ctx* c, int trial_steps, int* variant_out, int* ctas_per_
     c->dp.variant = best_v;
     c->dp.bgrid = best_k * c->nsm;
     rc = upload_work(c);
-    if (!rc) e = cudaMemcpyAsync(c->dp.F, saved, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (!rc) e = put_state(true);
   }
   if (t0) cudaEventDestroy(t0);
   if (t1) cudaEventDestroy(t1);

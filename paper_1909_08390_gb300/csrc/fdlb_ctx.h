@@ -29,9 +29,14 @@ struct fdlb_ctx {
   fdlb::BatchProblem* probs_dev = nullptr;
   fdlb::WorkItem* work_dev = nullptr;
   int nsm = 0;
-  // CUDA graph of kGraphSteps steps, captured on first use
+  // CUDA graphs of kGraphSteps steps, captured on first use; FDLB_MIXED
+  // contexts keep one per state buffer the steps start from (parity)
   cudaStream_t capture_stream = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  // FDLB_MIXED: the two state buffers {hi, lo}; the current one is
+  // pair[parity], the final stage writes pair[1 - parity]
+  float* pair[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int parity = 0;
   // adjoint: per-step forward states of one checkpoint segment, adjoint
   // work arrays and scalar accumulators (allocated on first use)
   void* adj_buf = nullptr;

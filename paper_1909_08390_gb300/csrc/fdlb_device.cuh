@@ -11,11 +11,12 @@
 
 #include "fdlb_internal.h"
 #include "fdlb_mp9.cuh"
+#include "fdlb_tile.cuh"
 
 namespace fdlb {
 namespace {
 
-constexpr int H = 5;  // ghost nodes per side (Sec. IV)
+constexpr int H = kGhost;  // ghost nodes per side (Sec. IV)
 
 template <int DIM, int VAR = 0>
 struct TileCfg;
@@ -90,14 +91,6 @@ struct Geo {
   double kchi, invDK, dtdx, dtdy;
   int prob;  // batch problem index, -1 for a single-problem context
 };
-
-__device__ __forceinline__ int wrap_or_clamp(int i, int n, int bc) {
-  if (bc == 1) {
-    i %= n;
-    return i < 0 ? i + n : i;
-  }
-  return i < 0 ? 0 : (i >= n ? n - 1 : i);
-}
 
 // One axis of the Hermite-expanded equilibrium (Eq. gExpanded):
 // g_k = sum_{l<Q} [w_k He_l(p_k)/l!] a_l(u, T) with

@@ -83,8 +83,18 @@ struct DevParams {
   int nprob, nwork;
   int variant;  // 1-D tile shape of the batch kernels (0, 1, 2)
   int bgrid;    // persistent grid size of the batch kernels
-  // FDLB_MIXED: per-cell records of the binary64 equilibrium factors, stored
-  // as binary32 (recw components x N each), of F^n, R3 and R4 (fdlb_mixed.cu)
+  // FDLB_MIXED (fdlb_mixed.cu).  Each population of the state is an
+  // unevaluated pair of binary32 values sh + sl (|sl| <= ulp(sh)/2), read
+  // from (sh, sl) and written by the final stage to (nh, nl), the two buffers
+  // swapping roles every step.  The stage arrays hold the binary32 low parts
+  // of the explicit parts relative to the state's high part: R3 = sh + r3l,
+  // A4' = sh + a4l (then R4 = sh + a4l), A_fin = sh + afl.  mhi[4][N] holds
+  // per cell the binary64 moment sums (n, jx, jy, e) of sh.  erec[3] are
+  // per-cell records of the equilibrium factors of F^n, R3 and R4, each
+  // component a binary32 pair: recw high parts, then recw low parts, N apart.
+  float *sh, *sl, *nh, *nl;
+  float *r3l, *a4l, *afl;
+  double* mhi;
   float* erec[3];
   int recw;
 };
@@ -117,5 +127,8 @@ int mixed_record_width(int d, int Qp, int Qc);
 int mixed_setup(const DevParams& p);
 int launch_mixed_stage(const DevParams& p, int stage, cudaStream_t s);
 int launch_mixed_batch_stage(const DevParams& p, int stage, cudaStream_t s);
+// the binary32-pair state of FDLB_MIXED contexts <-> binary64 values
+int launch_pair_to_double(const float* hi, const float* lo, double* out, int64_t n, cudaStream_t s);
+int launch_double_to_pair(const double* in, float* hi, float* lo, int64_t n, cudaStream_t s);
 
 }  // namespace fdlb

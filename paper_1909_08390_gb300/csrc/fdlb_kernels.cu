@@ -83,7 +83,6 @@ __device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, i
     // this thread's march task: population tg of the group, line, segment
     const int tg = tid / (NLINE * NSEG);
     const int tline = (tid / NSEG) % NLINE;
-    const int tseg = tid % NSEG;
     // this thread's staged cells (tile offset, cell offset from geo.base or
     // -1): ghosts by index clamp or wrap; the 2-D halo corners feed no line
     constexpr int SXH = TX + 2 * H;
@@ -127,20 +126,13 @@ __device__ __forceinline__ void stage_tile(const DevParams& p, const Geo& geo, i
         const bool xline = (DIM == 1) || (tline < TY);
         const double pv = (pop < L::P) ? (xline ? p.px[pop] : p.py[pop]) : 0.0;
         const int sgn = (pv >= 0.0) ? 1 : -1;
-        const int i0 = tseg * SEG;  // first interface of the segment (low index)
-        // interface i lies between tile cells i-1 and i; its upwind cell is
-        // i-1 for p >= 0 and i for p < 0 (mirror image, index s+j <-> s+1-j);
-        // tile cell c sits at column/row c + H.
-        const int first = (sgn > 0) ? i0 : i0 + SEG - 1;
-        const int up = ((sgn > 0) ? first - 1 : first) + H;
         // one call site for x and y lines (a warp holds both kinds): the line
-        // is (base, element stride) in the tile and its output row
-        const int r = (DIM == 2 && xline) ? tline : 0;  // x line: tile row
-        const int c = xline ? 0 : tline - TY;           // y line: tile column
-        const S* base = xline ? &tile[tg][r + (DIM == 2 ? H : 0)][up] : &tile[tg][up][c + H];
-        const int stride = xline ? 1 : SX;
-        S* out = xline ? &hx[tg][r][first] : &hy[tg][c][first];
-        mp9_march<SEG>(base, sgn * stride, out, sgn);
+        // is (base, signed element stride) in the tile and its output slots
+        // (march_task: interface i lies between tile cells i-1 and i, tile
+        // cell c at column/row c + H, mirror image for p < 0)
+        const MarchTask t = march_task(tid, DIM, TX, TY, SEG, SX, sgn);
+        S* out = t.xline ? &hx[tg][t.orow][t.ofirst] : &hy[tg][t.orow][t.ofirst];
+        mp9_march<SEG>(&tile[tg][t.br][t.bc_], t.stride, out, sgn);
       }
       __syncthreads();  // the march is done with the tile
       if (g0 + G < L::P) prefetch(g0 + G);
@@ -251,6 +243,26 @@ __global__ void __launch_bounds__(TileCfg<1, VAR>::NT)
   }
 }
 
+// Store the binary64 equilibrium of cell c as the state: binary64 values
+// (FDLB_FP64), or binary32 pairs hi + lo with hi the rounded value and lo
+// the rounded remainder (FDLB_MIXED).
+template <typename S, int DIM, int QP, int QC>
+__device__ __forceinline__ void store_state(const DevParams& p,
+                                            const EqCellS<DIM, QP, QC, double>& eq, int64_t c) {
+  using L = Lat<DIM, QP, QC>;
+#pragma unroll
+  for (int pop = 0; pop < L::P; ++pop) {
+    const double v = feq_of<DIM, QP, QC, double>(eq, pop);
+    if constexpr (sizeof(S) == 8) {
+      ((double*)p.F)[pop * p.N + c] = v;
+    } else {
+      const float h = (float)v;
+      p.sh[pop * p.N + c] = h;
+      p.sl[pop * p.N + c] = (float)(v - (double)h);
+    }
+  }
+}
+
 // problem of cell c (problems sorted by base)
 __device__ __forceinline__ int find_problem(const DevParams& p, int64_t c) {
   int lo = 0, hi = p.nprob - 1;
@@ -276,9 +288,7 @@ __global__ void batch_init_kernel(const __grid_constant__ DevParams p) {
   make_eq_nut<1, QP, QC>(p, bp.kchi, rho, ux, 0.0, P / rho, eq64);
   EqCellS<1, QP, QC, double> eq;
   to_storage(eq64, eq);
-  S* F = (S*)p.F;
-#pragma unroll
-  for (int pop = 0; pop < L::P; ++pop) F[pop * p.N + c] = (S)feq_of<1, QP, QC, double>(eq, pop);
+  store_state<S>(p, eq, c);
 }
 
 // Piecewise-constant Riemann data -> discrete equilibrium (Sec. V).
@@ -311,9 +321,27 @@ __global__ void init_riemann_kernel(const __grid_constant__ DevParams p,
   make_eq_nut<DIM, QP, QC>(p, p.kchi, rho, ux, uy, P / rho, eq64);
   EqCellS<DIM, QP, QC, double> eq;  // binary64 products, rounded once on store
   to_storage(eq64, eq);
-  S* F = (S*)p.F;
-#pragma unroll
-  for (int pop = 0; pop < L::P; ++pop) F[pop * p.N + c] = (S)feq_of<DIM, QP, QC, double>(eq, pop);
+  store_state<S>(p, eq, c);
+}
+
+// Moments of a binary32-pair state: the binary64 sums of the high parts
+// (mhi, kept by the stage kernels) plus binary64 sums of the low parts.
+template <int DIM, int QP, int QC>
+__global__ void mixed_moments_kernel(const __grid_constant__ DevParams p, double* __restrict__ n,
+                                     double* __restrict__ ux, double* __restrict__ uy,
+                                     double* __restrict__ T) {
+  using L = Lat<DIM, QP, QC>;
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.N) return;
+  Moments m = {p.mhi[c], p.mhi[p.N + c], p.mhi[2 * p.N + c], p.mhi[3 * p.N + c]};
+  for (int pop = 0; pop < L::P; ++pop) accumulate<DIM, QP, QC>(p, m, pop, (double)p.sl[pop * p.N + c]);
+  double nn, vx, vy, TT;
+  const double invDK = p.nprob > 0 ? p.probs[find_problem(p, c)].invDK : p.invDK;
+  moments_to_nut<DIM>(invDK, m, nn, vx, vy, TT);
+  n[c] = nn;
+  ux[c] = vx;
+  if (DIM == 2 && uy) uy[c] = vy;
+  T[c] = TT;
 }
 
 template <int DIM, int QP, int QC, typename S>
@@ -424,7 +452,7 @@ int launch_moments_t(const DevParams& p, double* n, double* ux, double* uy, doub
                      cudaStream_t s) {
   const int nt = 128;
   const int64_t nb = (p.N + nt - 1) / nt;
-  if (p.precision == 1) moments_kernel<DIM, QP, QC, float><<<(unsigned)nb, nt, 0, s>>>(p, n, ux, uy, T);
+  if (p.precision == 1) mixed_moments_kernel<DIM, QP, QC><<<(unsigned)nb, nt, 0, s>>>(p, n, ux, uy, T);
   else moments_kernel<DIM, QP, QC, double><<<(unsigned)nb, nt, 0, s>>>(p, n, ux, uy, T);
   return (int)cudaGetLastError();
 }

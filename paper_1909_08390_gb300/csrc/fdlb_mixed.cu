@@ -1,25 +1,40 @@
 // fdlb_mixed.cu -- binary32 stage kernels of the IMEX step (FDLB_MIXED):
 // one pass over memory per advected stage.
 //
-// The binary64 kernels (fdlb_kernels.cu) relax a stage in a second pass over
-// values parked in the output arrays, because the equilibrium of a cell needs
-// the moments of all its populations.  Here the relaxation of stage i is
-// applied by the kernel of stage i+1, when it loads the advected array:
-//   * every kernel writes the unrelaxed explicit part R_i of its stage, sums
-//     the moments of R_i per cell (Eq. Moments_discrete, compensated binary32
-//     pairs), and stores a record of the cell's equilibrium factors
-//     (Eq. gExpanded, in binary32-pair arithmetic of about 48 significant
-//     bits, each factor rounded once to binary32);
-//   * the next kernel forms the relaxed values from R_i and the record as it
-//     stages the tile and its halo (Sec. III closed forms):
-//       stage 3 stages F2 = E0 + c2 (F^n - E0) from F^n,
-//       stage 4 stages F3 = R3 - a33 e3 (R3 - E3) from R3,
-//       the final stage stages F4 = R4 - a44 e4 (R4 - E4) from R4,
-//     and uses D = F^n - E0, D3 = R3 - E3, D4 = R4 - E4 at its own cells.
-// Arrays read and written per population and step: stage 3 reads F^n and
-// writes R3, A4', Af'; stage 4 reads R3, A4', Af' and writes R4, Af''; the
-// final stage reads R4, Af'' and writes F^{n+1} -- 6 reads and 6 writes of
-// 4 bytes, plus one record per cell and kernel.
+// Storage.  Every population of the state F^n is an unevaluated pair of
+// binary32 values sh + sl with |sl| <= ulp(sh)/2 (about 48 significant
+// bits).  The explicit parts of the stages are kept as binary32 low parts
+// relative to sh (R3 = sh + r3l, A4' = sh + a4l, A_fin = sh + afl), which are
+// small where the flow is smooth, so their rounding is relative to the
+// increment and not to the population.  A binary32 copy of F rounded at each
+// stage loses about 6e-8 of every population per stage; over thousands of
+// steps that noise moves shocks and contacts by far more than the 1e-5 the
+// mixed path is held to.
+//
+// Each kernel relaxes the previous stage while it stages its advected
+// values (Sec. III closed forms), from per-cell records of the previous
+// stage's equilibrium factors (Eq. gExpanded, evaluated in binary32-pair
+// arithmetic and kept as pairs):
+//   stage 3 stages F2 = E0 + c2 D with D = F^n - E0,
+//   stage 4 stages F3 = R3 - a33 e3 D3 with D3 = R3 - E3,
+//   the final stage stages F4 = R4 - a44 e4 D4 with D4 = R4 - E4,
+// every D formed as (sh - Eh) + (low part - El), accurate to its own size.
+// On 2-D tiles the staged values are taken relative to one value per
+// population and tile (the state's sh at the tile's first cell): the MP-9
+// march is translation invariant, and the shift keeps its binary32 rounding
+// relative to the variation across the tile instead of to the populations.
+//
+// Moments (Eq. Moments_discrete) of R3 and R4 are the binary64 per-cell sums
+// of sh (mhi, from the previous final stage) plus binary32 sums of the low
+// parts; the final stage sums the new state's sh with error-free
+// transformations (TwoSum and the fma product error) and its sl plainly.
+// n, u and T (the cancellation T = (e - j u)/((D+K) n) included) are then
+// recovered in binary64, and the record of the next equilibrium is written.
+//
+// Arrays per population and step: stage 3 reads sh, sl and writes r3l, a4l,
+// afl; stage 4 reads sh, r3l, a4l, afl and writes a4l (now R4's low part)
+// and afl; the final stage reads sh, a4l, afl and writes the new nh, nl --
+// 16 binary32 accesses, plus the records and mhi per cell.
 #include "fdlb_device.cuh"
 
 namespace fdlb {
@@ -28,8 +43,10 @@ namespace {
 // Components of a cell's record.  phi^eq(kx, ky) = A[kx] * B[ky] with
 // A = n g_x, B = g_y (1-D: A[k]); chi^eq(qx, qy) = C * A[qx] * B[qy] with
 // C = (D+K-d) T when Qchi = Qphi, else Hx[qx] * Hy[qy] with Hx = nchi h_x.
-// 2-D records with Qchi = Qphi also hold CB[ky] = C B[ky] (each rounded once),
-// so that chi^eq = A[qx] * CB[qy] takes the same two factors as phi^eq.
+// 2-D records with Qchi = Qphi also hold CB[ky] = C B[ky], so that
+// chi^eq = A[qx] * CB[qy] takes the same two factors as phi^eq.  Every
+// component is a binary32 pair: high parts at components 0..W-1, low parts
+// at W..2W-1.
 template <int DIM, int QP, int QC>
 struct RecLayout {
   static constexpr bool kSame = QP == QC;
@@ -40,35 +57,10 @@ struct RecLayout {
   static_assert(!kCB || kCBo + QP == W, "CB components close the record");
 };
 
-// Equilibrium of population pop from a record whose components lie `stride`
-// floats apart (read through the read-only data cache).
-template <int DIM, int QP, int QC>
-__device__ __forceinline__ float eq_from_rec(const float* __restrict__ rec, int64_t stride,
-                                             int pop) {
-  using R = RecLayout<DIM, QP, QC>;
-  using L = Lat<DIM, QP, QC>;
-  if (pop < L::NPHI) {
-    if constexpr (DIM == 1) return rec[pop * stride];
-    else return rec[(pop % QP) * stride] * rec[(QP + pop / QP) * stride];
-  }
-  const int q = pop - L::NPHI;
-  if constexpr (R::kSame) {
-    if constexpr (DIM == 1) return rec[R::kChi * stride] * rec[q * stride];
-    else return rec[R::kChi * stride] * (rec[(q % QP) * stride] * rec[(QP + q / QP) * stride]);
-  } else {
-    if constexpr (DIM == 1) return rec[(R::kChi + q) * stride];
-    else return rec[(R::kChi + q % QC) * stride] * rec[(R::kChi + QC + q / QC) * stride];
-  }
-}
-
 // ---- binary32 pairs: x = hi + lo with about 48 significant bits ----------
-// The records' Hermite factors are evaluated in this arithmetic on the
-// binary32 pipe.  GB300's binary64 pipe runs at 1/64 of the binary32 rate;
-// evaluated in binary64, the factors of a 1-D cell (16 populations) would
-// cost more pipe time than all of the cell's population work.  The pair
-// arithmetic is the classical error-free one (Dekker, Knuth): TwoSum for
-// additions, the fused multiply-add for the exact product error; the
-// intrinsics keep the compiler from contracting the error terms away.
+// The classical error-free arithmetic (Dekker, Knuth): TwoSum for additions,
+// the fused multiply-add for the exact product error; the intrinsics keep
+// the compiler from contracting the error terms away.
 struct DF {
   float hi, lo;
 };
@@ -95,7 +87,6 @@ __device__ __forceinline__ DF df_of(double x) {
   const float h = (float)x;
   return {h, (float)(x - (double)h)};
 }
-__device__ __forceinline__ float df_round(DF x) { return __fadd_rn(x.hi, x.lo); }
 
 // The same pair arithmetic on two lanes at once (packed binary32, sm_100
 // and later); each lane performs exactly the operations of DF.
@@ -121,6 +112,23 @@ __device__ __forceinline__ DF2 df_mul2(DF2 x, DF2 y) {
   return df_quick2(pr, e);
 }
 __device__ __forceinline__ DF2 df_bcast(DF x) { return {f2s(x.hi), f2s(x.lo)}; }
+
+// Product of two pairs without renormalising (hi = x.hi y.hi rounded, lo the
+// rest to binary32 accuracy): an equilibrium population from its factors.
+__device__ __forceinline__ DF pmul(DF x, DF y) {
+  const float h = __fmul_rn(x.hi, y.hi);
+  float l = fmaf(x.hi, y.hi, -h);
+  l = fmaf(x.hi, y.lo, l);
+  l = fmaf(x.lo, y.hi, l);
+  return {h, l};
+}
+__device__ __forceinline__ DF2 pmul2(DF2 x, DF2 y) {
+  const float2 h = __fmul2_rn(x.hi, y.hi);
+  float2 l = __ffma2_rn(x.hi, y.hi, neg2(h));
+  l = __ffma2_rn(x.hi, y.lo, l);
+  l = __ffma2_rn(x.lo, y.hi, l);
+  return {h, l};
+}
 
 // One axis of the equilibrium factors (Eq. gExpanded) times `scale`, in pair
 // arithmetic: the recurrence a_0 = s, a_1 = s u, a_l = u a_{l-1} +
@@ -175,77 +183,94 @@ __device__ __forceinline__ void axis_g_df(const float* ch, const float* cl, DF u
 }
 
 // Record of the equilibrium of (n, u, T) at cell `cell` of rec (components N
-// apart), in pair arithmetic, each component rounded once to binary32.
+// apart, high parts then low parts), in pair arithmetic.
 template <int DIM, int QP, int QC>
 __device__ __forceinline__ void write_record(const DevParams& p, DF kchi, DF n, DF ux, DF uy, DF T,
                                              float* __restrict__ rec, int64_t cell, int64_t N) {
   using R = RecLayout<DIM, QP, QC>;
+  constexpr int W = R::W;
+  auto put = [&](int k, DF v) {
+    rec[k * N + cell] = v.hi;
+    rec[(W + k) * N + cell] = v.lo;
+  };
   const DF one{1.0f, 0.0f};
   DF g[QP];
   axis_g_df<QP>(p.wHph, p.wHpl, ux, T, n, g);
 #pragma unroll
-  for (int k = 0; k < QP; ++k) rec[k * N + cell] = df_round(g[k]);
+  for (int k = 0; k < QP; ++k) put(k, g[k]);
   if constexpr (DIM == 2) {
     axis_g_df<QP>(p.wHph, p.wHpl, uy, T, one, g);
 #pragma unroll
-    for (int k = 0; k < QP; ++k) rec[(QP + k) * N + cell] = df_round(g[k]);
+    for (int k = 0; k < QP; ++k) put(QP + k, g[k]);
   }
   const DF kT = df_mul(kchi, T);
   if constexpr (R::kSame) {
-    rec[R::kChi * N + cell] = df_round(kT);
+    put(R::kChi, kT);
     if constexpr (R::kCB) {  // g holds the y factors B
 #pragma unroll
-      for (int k = 0; k < QP; ++k) rec[(R::kCBo + k) * N + cell] = df_round(df_mul(kT, g[k]));
+      for (int k = 0; k < QP; ++k) put(R::kCBo + k, df_mul(kT, g[k]));
     }
   } else {
     DF h[QC];
     axis_g_df<QC>(p.wHch, p.wHcl, ux, T, df_mul(kT, n), h);
 #pragma unroll
-    for (int q = 0; q < QC; ++q) rec[(R::kChi + q) * N + cell] = df_round(h[q]);
+    for (int q = 0; q < QC; ++q) put(R::kChi + q, h[q]);
     if constexpr (DIM == 2) {
       axis_g_df<QC>(p.wHch, p.wHcl, uy, T, one, h);
 #pragma unroll
-      for (int q = 0; q < QC; ++q) rec[(R::kChi + QC + q) * N + cell] = df_round(h[q]);
+      for (int q = 0; q < QC; ++q) put(R::kChi + QC + q, h[q]);
     }
   }
 }
 
-// Moments of a cell -> validity flags and record: n, u = j/n and
-// T = (E - j u)/((D+K) n) (Eq. Moments_discrete and the temperature
-// definition) from the compensated sums, in pair arithmetic.  The reciprocal
-// is one Newton step from the binary32 one.
+// Moment sums (n, jx, jy, e) of a cell, binary64 -> validity flags and the
+// record of its equilibrium: u = j/n and T = (e - j.u)/((D+K) n) (Eq.
+// Moments_discrete and the temperature definition) in binary64, the Hermite
+// factors in pair arithmetic from the binary64 n, u, T.
 template <int DIM, int QP, int QC>
-__device__ __forceinline__ void finish_cell(const DevParams& p, DF kchi, DF invDK, int prob,
-                                            const MomentsF& m, float* __restrict__ rec,
-                                            int64_t cell) {
-  const DF zero{0.0f, 0.0f};
-  const DF n = df_add(DF{m.nh, 0.0f}, DF{m.nl, 0.0f});
-  const DF jx = df_add(DF{m.jxh, 0.0f}, DF{m.jxl, 0.0f});
-  const DF jy = DIM == 2 ? df_add(DF{m.jyh, 0.0f}, DF{m.jyl, 0.0f}) : zero;
-  const DF e = df_add(DF{m.eh, 0.0f}, DF{m.el, 0.0f});
-  const float r0 = __frcp_rn(n.hi);
-  const DF inv_n = df_add(DF{r0, 0.0f},
-                          df_mul(DF{r0, 0.0f}, df_add(DF{1.0f, 0.0f}, df_neg(df_mul(n, DF{r0, 0.0f})))));
-  const DF ux = df_mul(jx, inv_n);
-  const DF uy = DIM == 2 ? df_mul(jy, inv_n) : zero;
-  DF ke = df_add(e, df_neg(df_mul(jx, ux)));
-  if constexpr (DIM == 2) ke = df_add(ke, df_neg(df_mul(jy, uy)));
-  const DF T = df_mul(df_mul(ke, inv_n), invDK);
-  const bool ok = n.hi > 0.0f && T.hi > 0.0f && isfinite(n.hi) && isfinite(T.hi) &&
-                  isfinite(ux.hi) && isfinite(uy.hi);
+__device__ __forceinline__ void finish_cell(const DevParams& p, double kchi, double invDK, int prob,
+                                            double n, double jx, double jy, double e,
+                                            float* __restrict__ rec, int64_t cell) {
+  const double inv_n = 1.0 / n;
+  const double ux = jx * inv_n;
+  const double uy = DIM == 2 ? jy * inv_n : 0.0;
+  const double T = (e - fma(jx, ux, jy * uy)) * inv_n * invDK;
+  const bool ok = n > 0.0 && T > 0.0 && isfinite(n) && isfinite(T) && isfinite(ux) && isfinite(uy);
   if (!ok) {
     atomicOr(p.status, 1u);
     if (prob >= 0) atomicOr(&p.pstatus[prob], 1u);
   }
-  write_record<DIM, QP, QC>(p, kchi, n, ux, uy, T, rec, cell, p.N);
+  write_record<DIM, QP, QC>(p, df_of(kchi), df_of(n), df_of(ux), df_of(uy), df_of(T), rec, cell,
+                            p.N);
+}
+
+// Equilibrium pair of population pop from a record whose components lie
+// `stride` floats apart (read through the read-only data cache).
+template <int DIM, int QP, int QC>
+__device__ __forceinline__ DF eq_from_rec(const float* __restrict__ rec, int64_t stride, int pop) {
+  using R = RecLayout<DIM, QP, QC>;
+  using L = Lat<DIM, QP, QC>;
+  auto c = [&](int k) { return DF{rec[k * stride], rec[(R::W + k) * stride]}; };
+  if (pop < L::NPHI) {
+    if constexpr (DIM == 1) return c(pop);
+    else return pmul(c(pop % QP), c(QP + pop / QP));
+  }
+  const int q = pop - L::NPHI;
+  if constexpr (R::kSame) {
+    if constexpr (DIM == 1) return pmul(c(R::kChi), c(q));
+    else return pmul(c(q % QP), c(R::kCBo + q / QP));
+  } else {
+    if constexpr (DIM == 1) return c(R::kChi + q);
+    else return pmul(c(R::kChi + q % QC), c(R::kChi + QC + q / QC));
+  }
 }
 
 // Record prefetch plan of a population group, for lattices with Qchi = Qphi
 // whose groups align with rows of the velocity grid ((8, 8) with groups of 4
 // in 2-D; groups of 8 or 16 in 1-D).  Slot s of the group's buffer holds one
-// record component: slots 0..NA-1 the x factors A of the group's columns,
-// then slot kB the second factor: in 2-D B of the group's row (phi) or CB
-// (chi), in 1-D the chi factor C.
+// record component (its high and low parts): slots 0..NA-1 the x factors A
+// of the group's columns, then slot kB the second factor: in 2-D B of the
+// group's row (phi) or CB (chi), in 1-D the chi factor C.
 template <int DIM, int QP, int QC, int G>
 struct GroupRec {
   static constexpr bool kOn =
@@ -270,26 +295,80 @@ struct GroupRec {
   }
 };
 
+// First population of group gi.  2-D groups with a record plan run
+// x-block-major: the 8 groups that share the x factors A of one block of G
+// columns come one after another (rows ky = 0..QP-1), phi before chi, so that
+// only B (and C once) change from one group to the next.  Otherwise groups
+// run in population order.  The final stage and the prep kernel sum the
+// moments in this order, so that both give the same bits.
+template <int DIM, int QP, int QC, int G>
+__device__ __forceinline__ int group_pop(int gi) {
+  using L = Lat<DIM, QP, QC>;
+  if constexpr (DIM == 2 && GroupRec<DIM, QP, QC, G>::kOn) {
+    constexpr int per_half = L::NPHI / G;
+    const int half = gi / per_half, r = gi % per_half;
+    return half * L::NPHI + (r % QP) * QP + (r / QP) * G;
+  } else {
+    return gi * G;
+  }
+}
+
 template <int DIM, int QP, int QC, int VAR, int STAGE>
 struct MixSmem {
   using C = TileCfg<DIM, VAR>;
+  using GR = GroupRec<DIM, QP, QC, C::G>;
   static constexpr int SXH = C::TX + 2 * H;             // staged columns
   static constexpr int SX = SXH + (DIM == 2 ? 1 : 0);   // tile row pitch
   static constexpr int SY = DIM == 2 ? C::TY + 2 * H : 1;
   // staged cells: tile + halo without the 2-D corner blocks, which feed no
   // line (rows 0..H-1 and H+TY.. take the tile's columns only)
   static constexpr int NSC = DIM == 2 ? C::TY * SXH + 2 * H * C::TX : SXH;
-  float raw[C::G][NSC];                // the group's advected values as loaded
-  // the group's record components (GroupRec plan), as loaded
-  float rbuf[GroupRec<DIM, QP, QC, C::G>::kOn ? GroupRec<DIM, QP, QC, C::G>::NS : 1]
-            [GroupRec<DIM, QP, QC, C::G>::kOn ? NSC : 1];
-  float tile[C::G][SY][SX];            // relaxed advected populations
-  float hx[C::G][C::TY][C::TX + 1];    // interface values along x
-  float hy[DIM == 2 ? C::G : 1][DIM == 2 ? C::TX : 1][C::TY + 1];
+  static constexpr int NSL = GR::kOn ? GR::NS : 1;
+  float rawh[C::G][NSC];               // the state's high parts sh, as loaded
+  float rawl[C::G][NSC];               // the advected array's low parts, as loaded
+  float rbh[NSL][GR::kOn ? NSC : 1];   // the group's record components (GroupRec
+  float rbl[NSL][GR::kOn ? NSC : 1];   // plan): high and low parts, as loaded
+  float tile[C::G][SY][SX];            // relaxed advected populations - ref
+  // 2-D: flux differences of the cells along x and y (mp9_march_delta_fp32);
+  // 1-D: interface values along x
+  float hx[C::G][C::TY][C::TX + (DIM == 2 ? 0 : 1)];
+  float hy[DIM == 2 ? C::G : 1][DIM == 2 ? C::TX : 1][DIM == 2 ? C::TY : 1];
   float ownd[C::G][C::TY * C::TX];     // R - F_eq of the own cells
-  // stage 3 only: F^n of the own cells
-  float ownv[STAGE == kStage3 ? C::G : 1][STAGE == kStage3 ? C::TY * C::TX : 1];
+  // stage 3: sl of the own cells; final stage: sh of the own cells
+  float ownv[STAGE == kStage4 ? 1 : C::G][STAGE == kStage4 ? 1 : C::TY * C::TX];
 };
+
+// Plain binary32 moment sums of low parts (stages 3 and 4), two cells.
+struct MomL2 {
+  float2 n, jx, jy, e;
+};
+template <int DIM, int QP, int QC>
+__device__ __forceinline__ void accum_low2(const DevParams& p, MomL2& m, int pop, float2 v) {
+  using L = Lat<DIM, QP, QC>;
+  if (pop < L::NPHI) {
+    m.n = __fadd2_rn(m.n, v);
+    m.jx = __ffma2_rn(f2s(p.pxh[pop]), v, m.jx);
+    if (DIM == 2) m.jy = __ffma2_rn(f2s(p.pyh[pop]), v, m.jy);
+    m.e = __ffma2_rn(f2s(p.p2h[pop]), v, m.e);
+  } else {
+    m.e = __fadd2_rn(m.e, v);
+  }
+}
+struct MomL {
+  float n, jx, jy, e;
+};
+template <int DIM, int QP, int QC>
+__device__ __forceinline__ void accum_low(const DevParams& p, MomL& m, int pop, float v) {
+  using L = Lat<DIM, QP, QC>;
+  if (pop < L::NPHI) {
+    m.n = __fadd_rn(m.n, v);
+    m.jx = fmaf(p.pxh[pop], v, m.jx);
+    if (DIM == 2) m.jy = fmaf(p.pyh[pop], v, m.jy);
+    m.e = fmaf(p.p2h[pop], v, m.e);
+  } else {
+    m.e = __fadd_rn(m.e, v);
+  }
+}
 
 // One tile of one stage.  Ends with every thread past its last use of the
 // shared memory, so a persistent CTA may start its next tile at once.
@@ -299,6 +378,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   using C = TileCfg<DIM, VAR>;
   using L = Lat<DIM, QP, QC>;
   using M = MixSmem<DIM, QP, QC, VAR, STAGE>;
+  using R = RecLayout<DIM, QP, QC>;
   constexpr int TX = C::TX, TY = C::TY, NT = C::NT, G = C::G, SEG = C::SEG;
   constexpr int SX = M::SX, SXH = M::SXH, NSC = M::NSC;
   constexpr int CELLS = TX * TY;
@@ -308,15 +388,16 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   constexpr int NLINE = DIM == 2 ? TX + TY : 1;
   static_assert(G * NLINE * NSEG == NT, "one march task per thread");
   constexpr int J = (NSC + NT - 1) / NT;  // staged cells per thread
+  constexpr int W = R::W;
 
-  float* __restrict__ const F = (float*)p.F;
-  float* __restrict__ const R3 = (float*)p.F3;
-  float* __restrict__ const A4 = (float*)p.A4;
-  float* __restrict__ const Af = (float*)p.Af;
+  const float* __restrict__ const Sh = p.sh;
+  // the advected array's low parts: sl (stage 3), r3l (stage 4), a4l = R4's
+  // low part (final stage)
+  const float* __restrict__ const adv_l =
+      STAGE == kStage3 ? p.sl : (STAGE == kStage4 ? p.r3l : p.a4l);
   const float* __restrict__ const rin =
       p.erec[STAGE == kStage3 ? 0 : (STAGE == kStage4 ? 1 : 2)];
   float* __restrict__ const rout = p.erec[STAGE == kStage3 ? 1 : (STAGE == kStage4 ? 2 : 0)];
-  const float* __restrict__ const adv = STAGE == kStage3 ? F : (STAGE == kStage4 ? R3 : A4);
   const int tid = threadIdx.x;
   const int64_t N = p.N;
 
@@ -326,22 +407,9 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const int e = tid + j * NT;
-    // staged cell e (NSC of them): 2-D in three blocks -- rows above the tile
-    // (tile columns only), the tile's rows with both side halos, rows below
+    // staged cell e (NSC of them), in the compact order of staged_pos
     int r, c;
-    if (DIM == 1) {
-      r = 0;
-      c = e;
-    } else if (e < H * TX) {
-      r = e / TX;
-      c = H + e % TX;
-    } else if (e < H * TX + TY * SXH) {
-      r = H + (e - H * TX) / SXH;
-      c = (e - H * TX) % SXH;
-    } else {
-      r = H + TY + (e - H * TX - TY * SXH) / TX;
-      c = H + (e - H * TX - TY * SXH) % TX;
-    }
+    staged_pos(e, DIM, TX, TY, r, c);
     soff[j] = r * SX + c;
     goff[j] = -1;
     oidx[j] = -1;
@@ -360,56 +428,76 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   bool valid[CPT];
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
-    const int c = tid + k * NT;
+    // a slot past the tile's cells takes cell 0's indices (its lane computes
+    // on them and stores nothing), so every shared-memory index stays inside
+    // its array
+    const int c = tid + k * NT < CELLS ? tid + k * NT : 0;
     lxs[k] = c % TX;
     lys[k] = c / TX;
-    valid[k] = (c < CELLS) && (x0 + lxs[k] < geo.nx) && (y0 + lys[k] < geo.ny);
+    valid[k] = (tid + k * NT < CELLS) && (x0 + lxs[k] < geo.nx) && (y0 + lys[k] < geo.ny);
     cell[k] = geo.base + (int64_t)(y0 + lys[k]) * geo.nx + (x0 + lxs[k]);
   }
+  // moment sums: stages 3 and 4 sum the low parts plainly; the final stage
+  // sums the new high parts error-free (mom*) and the new low parts plainly
+  MomL lm[CPT];
   MomentsF mom[CPT];
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) mom[k] = {};
-  MomentsF2 mom2 = {};  // the two cells' sums when CPT == 2
+  for (int k = 0; k < CPT; ++k) {
+    lm[k] = {};
+    mom[k] = {};
+  }
+  MomL2 lm2 = {};
+  MomentsF2 mom2 = {};
   const CoefS<float> sc(p.sc);
   const float arelax = STAGE == kStage3 ? sc.c2 : (STAGE == kStage4 ? sc.a33e3 : sc.a44e4);
-  const float dtdx = (float)geo.dtdx, dtdy = (float)geo.dtdy;
-  const DF kchi_df = df_of(geo.kchi), invDK_df = df_of(geo.invDK);
+  // coefficients that multiply advection terms of the size of the
+  // populations' variation, as binary32 pairs: dt p / ds (a rounded speed
+  // would shift every wave coherently) and the explicit weights wt2, wt3,
+  // wt4 (1/6, 1/6, 2/3, whose rounded sum misses 1)
+  const DF dtdx_df = df_of(geo.dtdx), dtdy_df = df_of(geo.dtdy);
+  const float wtl = STAGE == kStage3 ? (float)(p.sc.wt2 - (double)sc.wt2)
+                  : STAGE == kStage4 ? (float)(p.sc.wt3 - (double)sc.wt3)
+                                     : (float)(p.sc.wt4 - (double)sc.wt4);
+  // dt p / ds of population pop along x or y as a pair; 2-D takes |.| (the
+  // flux differences of the 2-D march carry the velocity's sign)
+  auto coef = [&](int pop, bool x) {
+    DF c = df_mul(x ? dtdx_df : dtdy_df, x ? DF{p.pxh[pop], p.pxl[pop]} : DF{p.pyh[pop], p.pyl[pop]});
+    if (DIM == 2 && c.hi < 0.0f) c = df_neg(c);
+    return c;
+  };
   const float* __restrict__ const rbase = rin + geo.base;
+  // the reference value of each population on a 2-D tile: sh at the tile's
+  // first cell.  1-D tiles take none, so that a 1-D problem gives the same
+  // bits whatever its tiling (batches and single problems use different
+  // tile lengths).
+  const int64_t cref = geo.base + (int64_t)y0 * geo.nx + x0;
 
-  const int tg = tid / (NLINE * NSEG);
+  const int tg = tid / (NLINE * NSEG);  // the thread's population in a group (march)
   const int tline = (tid / NSEG) % NLINE;
-  const int tseg = tid % NSEG;
   // each thread copies, and later reads, only its own staged cells, so its
   // own wait on the copies orders them
   using GR = GroupRec<DIM, QP, QC, G>;
-  // Group order.  2-D groups with a record plan run x-block-major: the 8
-  // groups that share the x factors A of one block of G columns come one
-  // after another (rows ky = 0..QP-1), phi before chi, so that only B (and C
-  // once) change from one group to the next.  Otherwise groups run in
-  // population order.
   constexpr int NG = (L::P + G - 1) / G;
-  auto gpop = [](int gi) -> int {
-    if constexpr (DIM == 2 && GR::kOn) {
-      constexpr int per_half = L::NPHI / G;
-      const int half = gi / per_half, r = gi % per_half;
-      return half * L::NPHI + (r % QP) * QP + (r / QP) * G;
-    } else {
-      return gi * G;
-    }
-  };
-  // record component held by each slot of sm.rbuf (the same in every thread)
+  // record component held by each slot of the record buffers (the same in
+  // every thread)
   int rcomp[GR::kOn ? GR::NS : 1];
 #pragma unroll
   for (int sl = 0; sl < (GR::kOn ? GR::NS : 1); ++sl) rcomp[sl] = -1;
+  float refv[G];
   auto prefetch = [&](int gfirst) {
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int pop = gfirst + g;
       if (pop >= L::P) break;
-      const float* __restrict__ src = adv + (int64_t)pop * N + geo.base;
+      const float* __restrict__ srch = Sh + (int64_t)pop * N + geo.base;
+      const float* __restrict__ srcl = adv_l + (int64_t)pop * N + geo.base;
 #pragma unroll
       for (int j = 0; j < J; ++j)
-        if (goff[j] >= 0) cp_async(&sm.raw[g][tid + j * NT], src + goff[j]);
+        if (goff[j] >= 0) {
+          cp_async(&sm.rawh[g][tid + j * NT], srch + goff[j]);
+          cp_async(&sm.rawl[g][tid + j * NT], srcl + goff[j]);
+        }
+      refv[g] = DIM == 2 ? Sh[(int64_t)pop * N + cref] : 0.0f;
     }
     if constexpr (GR::kOn) {
 #pragma unroll
@@ -417,17 +505,21 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
         const int comp = GR::comp(gfirst, sl);
         if (comp < 0 || comp == rcomp[sl]) continue;  // absent, or still there
         rcomp[sl] = comp;
-        const float* __restrict__ src = rbase + (int64_t)comp * N;
+        const float* __restrict__ srch = rbase + (int64_t)comp * N;
+        const float* __restrict__ srcl = rbase + (int64_t)(W + comp) * N;
 #pragma unroll
         for (int j = 0; j < J; ++j)
-          if (goff[j] >= 0) cp_async(&sm.rbuf[sl][tid + j * NT], src + goff[j]);
+          if (goff[j] >= 0) {
+            cp_async(&sm.rbh[sl][tid + j * NT], srch + goff[j]);
+            cp_async(&sm.rbl[sl][tid + j * NT], srcl + goff[j]);
+          }
       }
     }
     cp_async_commit();
   };
-  prefetch(gpop(0));
+  prefetch(group_pop<DIM, QP, QC, G>(0));
   for (int gi = 0; gi < NG; ++gi) {
-    const int g0 = gpop(gi);  // first population of the group
+    const int g0 = group_pop<DIM, QP, QC, G>(gi);  // first population of the group
     // the running explicit parts of the own cells (stage 4, final), early
     float a4v[CPT][G], afv[CPT][G];
     if constexpr (STAGE != kStage3) {
@@ -438,28 +530,35 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
           const int pop = g0 + g;
           const bool ok = valid[k] && pop < L::P;
           const int64_t e = (int64_t)pop * N + cell[k];
-          a4v[k][g] = (STAGE == kStage4 && ok) ? A4[e] : 0.0f;
-          afv[k][g] = ok ? Af[e] : 0.0f;
+          a4v[k][g] = (STAGE == kStage4 && ok) ? p.a4l[e] : 0.0f;
+          afv[k][g] = ok ? p.afl[e] : 0.0f;
         }
     }
-    // ---- stage the group: relaxed advected values on tile + halo
+    // ---- stage the group: relaxed advected values - ref on tile + halo
     cp_async_wait_all();
-    // The equilibrium is A B (phi) or A CB (chi) from the record slots in
-    // 2-D, A (phi) or C A (chi) in 1-D,
-    // D = R - F_eq, and stage 3 stages F2 = E0 + c2 D, stages 4 and final
-    // F = R - a_ii e_i D; every operation is rounded on its own, so the
-    // paired (packed) and single forms below agree bit for bit.
-    auto keep = [&](int g, int j, float w, float d, float v) {
+    // With a = sh, b the advected low part and E = Eh + El the equilibrium
+    // pair: D = (a - Eh) + (b - El); stage 3 stages F2 - ref = (Eh - ref) +
+    // (El + c2 D), stages 4 and final F - ref = (a - ref) + (b - a_ii e_i D).
+    // Every operation is rounded on its own, so the paired (packed) and
+    // single forms below agree bit for bit.
+    auto keep = [&](int g, int j, float w, float d, float a, float b) {
       (&sm.tile[g][0][0])[soff[j]] = w;
       if (oidx[j] >= 0) {
         sm.ownd[g][oidx[j]] = d;
-        if constexpr (STAGE == kStage3) sm.ownv[g][oidx[j]] = v;
+        if constexpr (STAGE == kStage3) sm.ownv[g][oidx[j]] = b;
+        if constexpr (STAGE == kFinal) sm.ownv[g][oidx[j]] = a;
       }
+    };
+    auto relax1 = [&](float a, float b, DF E, float ref, float& d) {
+      d = __fadd_rn(__fsub_rn(a, E.hi), __fsub_rn(b, E.lo));
+      return STAGE == kStage3 ? __fadd_rn(__fsub_rn(E.hi, ref), fmaf(arelax, d, E.lo))
+                              : __fadd_rn(__fsub_rn(a, ref), fmaf(-arelax, d, b));
     };
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int pop = g0 + g;
       if (pop >= L::P) break;
+      const float ref = refv[g];
       if constexpr (GR::kOn) {
         const int nphi = DIM == 2 ? QP * QP : QP;
         const bool chi = pop >= nphi;
@@ -473,58 +572,66 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
           const bool ok0 = goff[j] >= 0, ok1 = goff[j + 1] >= 0;
           const int e0 = tid + j * NT;
           const int e1 = (j + 2) * NT > NSC ? min(tid + (j + 1) * NT, NSC - 1) : tid + (j + 1) * NT;
-          const float2 v = make_float2(sm.raw[g][e0], sm.raw[g][e1]);
-          float2 fe = make_float2(sm.rbuf[ia][e0], sm.rbuf[ia][e1]);
-          if constexpr (DIM == 2)
-            fe = __fmul2_rn(fe, make_float2(sm.rbuf[GR::kB][e0], sm.rbuf[GR::kB][e1]));
-          else if (chi)
-            fe = __fmul2_rn(make_float2(sm.rbuf[GR::kB][e0], sm.rbuf[GR::kB][e1]), fe);
-          const float2 d = sub2(v, fe);
-          const float2 w = STAGE == kStage3 ? __ffma2_rn(f2s(arelax), d, fe)
-                                            : __ffma2_rn(f2s(-arelax), d, v);
-          if (ok0) keep(g, j, w.x, d.x, v.x);
-          if (ok1) keep(g, j + 1, w.y, d.y, v.y);
+          const float2 a = make_float2(sm.rawh[g][e0], sm.rawh[g][e1]);
+          const float2 b = make_float2(sm.rawl[g][e0], sm.rawl[g][e1]);
+          const DF2 A = {make_float2(sm.rbh[ia][e0], sm.rbh[ia][e1]),
+                         make_float2(sm.rbl[ia][e0], sm.rbl[ia][e1])};
+          DF2 E = A;
+          if (DIM == 2 || chi) {
+            const DF2 B = {make_float2(sm.rbh[GR::kB][e0], sm.rbh[GR::kB][e1]),
+                           make_float2(sm.rbl[GR::kB][e0], sm.rbl[GR::kB][e1])};
+            E = pmul2(A, B);
+          }
+          const float2 d = __fadd2_rn(sub2(a, E.hi), sub2(b, E.lo));
+          const float2 w = STAGE == kStage3
+                               ? __fadd2_rn(sub2(E.hi, f2s(ref)), __ffma2_rn(f2s(arelax), d, E.lo))
+                               : __fadd2_rn(sub2(a, f2s(ref)), __ffma2_rn(f2s(-arelax), d, b));
+          if (ok0) keep(g, j, w.x, d.x, a.x, b.x);
+          if (ok1) keep(g, j + 1, w.y, d.y, a.y, b.y);
         }
         if constexpr (J % 2 == 1) {
           constexpr int j = J - 1;
           if (goff[j] >= 0) {
             const int e = tid + j * NT;
-            const float v = sm.raw[g][e];
-            float fe = sm.rbuf[ia][e];
-            if constexpr (DIM == 2) fe = __fmul_rn(fe, sm.rbuf[GR::kB][e]);
-            else if (chi) fe = __fmul_rn(sm.rbuf[GR::kB][e], fe);
-            const float d = __fsub_rn(v, fe);
-            keep(g, j, STAGE == kStage3 ? fmaf(arelax, d, fe) : fmaf(-arelax, d, v), d, v);
+            const float a = sm.rawh[g][e], b = sm.rawl[g][e];
+            DF E = {sm.rbh[ia][e], sm.rbl[ia][e]};
+            if (DIM == 2 || chi) E = pmul(E, DF{sm.rbh[GR::kB][e], sm.rbl[GR::kB][e]});
+            float d;
+            const float w = relax1(a, b, E, ref, d);
+            keep(g, j, w, d, a, b);
           }
         }
       } else {
 #pragma unroll
         for (int j = 0; j < J; ++j) {
           if (goff[j] < 0) continue;
-          const float v = sm.raw[g][tid + j * NT];
-          const float fe = eq_from_rec<DIM, QP, QC>(rbase + goff[j], N, pop);
-          const float d = __fsub_rn(v, fe);
-          keep(g, j, STAGE == kStage3 ? fmaf(arelax, d, fe) : fmaf(-arelax, d, v), d, v);
+          const float a = sm.rawh[g][tid + j * NT], b = sm.rawl[g][tid + j * NT];
+          const DF E = eq_from_rec<DIM, QP, QC>(rbase + goff[j], N, pop);
+          float d;
+          const float w = relax1(a, b, E, ref, d);
+          keep(g, j, w, d, a, b);
         }
       }
     }
     __syncthreads();
-    if (gi + 1 < NG) prefetch(gpop(gi + 1));  // overlaps the march and pass 1
+    if (gi + 1 < NG) prefetch(group_pop<DIM, QP, QC, G>(gi + 1));  // overlaps the march and pass 1
     // ---- every interface value once, marching upwind -> downwind
     {
       const int pop = g0 + tg;
       const bool xline = (DIM == 1) || (tline < TY);
       const float pv = (pop < L::P) ? (xline ? p.pxh[pop] : p.pyh[pop]) : 0.0f;
       const int sgn = (pv >= 0.0f) ? 1 : -1;
-      const int i0 = tseg * SEG;
-      const int first = (sgn > 0) ? i0 : i0 + SEG - 1;
-      const int up = ((sgn > 0) ? first - 1 : first) + H;
-      const int r = (DIM == 2 && xline) ? tline : 0;
-      const int c = xline ? 0 : tline - TY;
-      const float* base = xline ? &sm.tile[tg][r + (DIM == 2 ? H : 0)][up] : &sm.tile[tg][up][c + H];
-      const int stride = xline ? 1 : SX;
-      float* out = xline ? &sm.hx[tg][r][first] : &sm.hy[tg][c][first];
-      mp9_march<SEG>(base, sgn * stride, out, sgn);
+      const MarchTask t = march_task(tid, DIM, TX, TY, SEG, SX, sgn);
+      if constexpr (DIM == 2) {
+        // one segment per line: the flux differences of its cells, the first
+        // (in march order) one slot upwind of the first interface's slot
+        // when marching downwards
+        const int c0 = sgn > 0 ? t.ofirst : t.ofirst - 1;
+        float* out = t.xline ? &sm.hx[tg][t.orow][c0] : &sm.hy[tg][t.orow][c0];
+        mp9_march_delta_fp32<SEG>(&sm.tile[tg][t.br][t.bc_], t.stride, out, sgn);
+      } else {
+        mp9_march<SEG>(&sm.tile[tg][t.br][t.bc_], t.stride, &sm.hx[tg][t.orow][t.ofirst], sgn);
+      }
     }
     __syncthreads();
     // ---- flux difference and explicit part of the own cells
@@ -536,88 +643,141 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
       for (int g = 0; g < G; ++g) {
         const int pop = g0 + g;
         if (pop >= L::P) break;
-        const float2 dfx = sub2(make_float2(sm.hx[g][lys[0]][lxs[0] + 1], sm.hx[g][lys[1]][lxs[1] + 1]),
-                                make_float2(sm.hx[g][lys[0]][lxs[0]], sm.hx[g][lys[1]][lxs[1]]));
-        float2 X = __fmul2_rn(f2s(dtdx * p.pxh[pop]), dfx);
+        float2 X;
+        const DF cx = coef(pop, true);
         if constexpr (DIM == 2) {
-          const float2 dfy = sub2(make_float2(sm.hy[g][lxs[0]][lys[0] + 1], sm.hy[g][lxs[1]][lys[1] + 1]),
-                                  make_float2(sm.hy[g][lxs[0]][lys[0]], sm.hy[g][lxs[1]][lys[1]]));
-          X = __ffma2_rn(f2s(dtdy * p.pyh[pop]), dfy, X);
+          const DF cy = coef(pop, false);
+          const float2 dx = make_float2(sm.hx[g][lys[0]][lxs[0]], sm.hx[g][lys[1]][lxs[1]]);
+          const float2 dy = make_float2(sm.hy[g][lxs[0]][lys[0]], sm.hy[g][lxs[1]][lys[1]]);
+          X = __ffma2_rn(f2s(cx.hi), dx, __fmul2_rn(f2s(cx.lo), dx));
+          X = __ffma2_rn(f2s(cy.hi), dy, __ffma2_rn(f2s(cy.lo), dy, X));
+        } else {
+          const float2 dfx = sub2(make_float2(sm.hx[g][lys[0]][lxs[0] + 1], sm.hx[g][lys[1]][lxs[1] + 1]),
+                                  make_float2(sm.hx[g][lys[0]][lxs[0]], sm.hx[g][lys[1]][lxs[1]]));
+          X = __ffma2_rn(f2s(cx.hi), dfx, __fmul2_rn(f2s(cx.lo), dfx));
         }
         const int64_t e0 = (int64_t)pop * N + cell[0], e1 = (int64_t)pop * N + cell[1];
         const float2 d = make_float2(sm.ownd[g][o0], sm.ownd[g][o1]);
-        float2 R;
         if constexpr (STAGE == kStage3) {
-          const float2 f = make_float2(sm.ownv[g][o0], sm.ownv[g][o1]);
-          R = __ffma2_rn(f2s(-sc.at32), X, __ffma2_rn(f2s(-sc.k3), d, f));
-          const float2 a4 = __ffma2_rn(f2s(-sc.at42), X, __ffma2_rn(f2s(-sc.k4), d, f));
-          const float2 af = __ffma2_rn(f2s(-sc.wt2), X, __ffma2_rn(f2s(-sc.kf), d, f));
-          if (valid[0]) { R3[e0] = R.x; A4[e0] = a4.x; Af[e0] = af.x; }
-          if (valid[1]) { R3[e1] = R.y; A4[e1] = a4.y; Af[e1] = af.y; }
+          const float2 l = make_float2(sm.ownv[g][o0], sm.ownv[g][o1]);  // sl
+          const float2 r3 = __fadd2_rn(l, __ffma2_rn(f2s(-sc.at32), X, __fmul2_rn(f2s(-sc.k3), d)));
+          const float2 a4 = __fadd2_rn(l, __ffma2_rn(f2s(-sc.at42), X, __fmul2_rn(f2s(-sc.k4), d)));
+          const float2 af = __fadd2_rn(
+              l, __ffma2_rn(f2s(-sc.wt2), X, __ffma2_rn(f2s(-wtl), X, __fmul2_rn(f2s(-sc.kf), d))));
+          if (valid[0]) { p.r3l[e0] = r3.x; p.a4l[e0] = a4.x; p.afl[e0] = af.x; }
+          if (valid[1]) { p.r3l[e1] = r3.y; p.a4l[e1] = a4.y; p.afl[e1] = af.y; }
+          accum_low2<DIM, QP, QC>(p, lm2, pop, r3);
         } else if constexpr (STAGE == kStage4) {
-          R = __ffma2_rn(f2s(-sc.at43), X,
-                         __ffma2_rn(f2s(-sc.a43e3), d, make_float2(a4v[0][g], a4v[1][g])));
-          const float2 af = __ffma2_rn(f2s(-sc.wt3), X,
-                                       __ffma2_rn(f2s(-sc.w3e3), d, make_float2(afv[0][g], afv[1][g])));
-          if (valid[0]) { A4[e0] = R.x; Af[e0] = af.x; }
-          if (valid[1]) { A4[e1] = R.y; Af[e1] = af.y; }
+          const float2 r4 = __ffma2_rn(f2s(-sc.at43), X,
+                                       __ffma2_rn(f2s(-sc.a43e3), d, make_float2(a4v[0][g], a4v[1][g])));
+          const float2 af = __ffma2_rn(
+              f2s(-sc.wt3), X,
+              __ffma2_rn(f2s(-wtl), X,
+                         __ffma2_rn(f2s(-sc.w3e3), d, make_float2(afv[0][g], afv[1][g]))));
+          if (valid[0]) { p.a4l[e0] = r4.x; p.afl[e0] = af.x; }
+          if (valid[1]) { p.a4l[e1] = r4.y; p.afl[e1] = af.y; }
+          accum_low2<DIM, QP, QC>(p, lm2, pop, r4);
         } else {
-          R = __ffma2_rn(f2s(-sc.wt4), X,
-                         __ffma2_rn(f2s(-sc.w4e4), d, make_float2(afv[0][g], afv[1][g])));
-          if (valid[0]) F[e0] = R.x;
-          if (valid[1]) F[e1] = R.y;
+          // F^{n+1} = sh + t with t = afl - w4 e4 D4 - wt4 X4, renormalised by
+          // TwoSum into the next buffer
+          const float2 t = __ffma2_rn(
+              f2s(-sc.wt4), X,
+              __ffma2_rn(f2s(-wtl), X,
+                         __ffma2_rn(f2s(-sc.w4e4), d, make_float2(afv[0][g], afv[1][g]))));
+          const float2 a = make_float2(sm.ownv[g][o0], sm.ownv[g][o1]);  // sh
+          const float2 s = __fadd2_rn(a, t);
+          const float2 bb = sub2(s, a);
+          const float2 er = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(t, bb));
+          if (valid[0]) { p.nh[e0] = s.x; p.nl[e0] = er.x; }
+          if (valid[1]) { p.nh[e1] = s.y; p.nl[e1] = er.y; }
+          accumulate2<DIM, QP, QC>(p, mom2, pop, s);
+          accum_low2<DIM, QP, QC>(p, lm2, pop, er);
         }
-        accumulate2<DIM, QP, QC>(p, mom2, pop, R);
       }
     } else {
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-      if (!valid[k]) continue;
-      const int lx = lxs[k], ly = lys[k], o = ly * TX + lx;
+      for (int k = 0; k < CPT; ++k) {
+        if (!valid[k]) continue;
+        const int lx = lxs[k], ly = lys[k], o = ly * TX + lx;
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const int pop = g0 + g;
-        if (pop >= L::P) break;
-        float X = (dtdx * p.pxh[pop]) * (sm.hx[g][ly][lx + 1] - sm.hx[g][ly][lx]);
-        if constexpr (DIM == 2)
-          X = fmaf(dtdy * p.pyh[pop], sm.hy[g][lx][ly + 1] - sm.hy[g][lx][ly], X);
-        const int64_t e = (int64_t)pop * N + cell[k];
-        const float d = sm.ownd[g][o];
-        float R;
-        if constexpr (STAGE == kStage3) {
-          const float f = sm.ownv[g][o];
-          R = fmaf(-sc.at32, X, fmaf(-sc.k3, d, f));
-          R3[e] = R;
-          A4[e] = fmaf(-sc.at42, X, fmaf(-sc.k4, d, f));
-          Af[e] = fmaf(-sc.wt2, X, fmaf(-sc.kf, d, f));
-        } else if constexpr (STAGE == kStage4) {
-          R = fmaf(-sc.at43, X, fmaf(-sc.a43e3, d, a4v[k][g]));
-          A4[e] = R;
-          Af[e] = fmaf(-sc.wt3, X, fmaf(-sc.w3e3, d, afv[k][g]));
-        } else {
-          R = fmaf(-sc.wt4, X, fmaf(-sc.w4e4, d, afv[k][g]));
-          F[e] = R;
+        for (int g = 0; g < G; ++g) {
+          const int pop = g0 + g;
+          if (pop >= L::P) break;
+          float X;
+          const DF cx = coef(pop, true);
+          if constexpr (DIM == 2) {
+            const DF cy = coef(pop, false);
+            const float dx = sm.hx[g][ly][lx], dy = sm.hy[g][lx][ly];
+            X = fmaf(cx.hi, dx, __fmul_rn(cx.lo, dx));
+            X = fmaf(cy.hi, dy, fmaf(cy.lo, dy, X));
+          } else {
+            const float dfx = __fsub_rn(sm.hx[g][ly][lx + 1], sm.hx[g][ly][lx]);
+            X = fmaf(cx.hi, dfx, __fmul_rn(cx.lo, dfx));
+          }
+          const int64_t e = (int64_t)pop * N + cell[k];
+          const float d = sm.ownd[g][o];
+          if constexpr (STAGE == kStage3) {
+            const float l = sm.ownv[g][o];
+            const float r3 = __fadd_rn(l, fmaf(-sc.at32, X, __fmul_rn(-sc.k3, d)));
+            p.r3l[e] = r3;
+            p.a4l[e] = __fadd_rn(l, fmaf(-sc.at42, X, __fmul_rn(-sc.k4, d)));
+            p.afl[e] = __fadd_rn(l, fmaf(-sc.wt2, X, fmaf(-wtl, X, __fmul_rn(-sc.kf, d))));
+            accum_low<DIM, QP, QC>(p, lm[k], pop, r3);
+          } else if constexpr (STAGE == kStage4) {
+            const float r4 = fmaf(-sc.at43, X, fmaf(-sc.a43e3, d, a4v[k][g]));
+            p.a4l[e] = r4;
+            p.afl[e] = fmaf(-sc.wt3, X, fmaf(-wtl, X, fmaf(-sc.w3e3, d, afv[k][g])));
+            accum_low<DIM, QP, QC>(p, lm[k], pop, r4);
+          } else {
+            const float t = fmaf(-sc.wt4, X, fmaf(-wtl, X, fmaf(-sc.w4e4, d, afv[k][g])));
+            const float a = sm.ownv[g][o];
+            const float s = __fadd_rn(a, t);
+            const float bb = __fsub_rn(s, a);
+            const float er = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(t, bb));
+            p.nh[e] = s;
+            p.nl[e] = er;
+            accumulate<DIM, QP, QC>(p, mom[k], pop, s);
+            accum_low<DIM, QP, QC>(p, lm[k], pop, er);
+          }
         }
-        accumulate<DIM, QP, QC>(p, mom[k], pop, R);
       }
-    }
     }
     __syncthreads();
   }
   if constexpr (CPT == 2) {
+    lm[0] = MomL{lm2.n.x, lm2.jx.x, lm2.jy.x, lm2.e.x};
+    lm[1] = MomL{lm2.n.y, lm2.jx.y, lm2.jy.y, lm2.e.y};
     mom[0] = lane(mom2, 0);
     mom[1] = lane(mom2, 1);
   }
-  // ---- records of the stage's explicit parts (the next kernel relaxes them)
+  // ---- per cell: binary64 moments of the stage's explicit part (or of the
+  // new state) and the record of its equilibrium (the next kernel relaxes)
 #pragma unroll
-  for (int k = 0; k < CPT; ++k)
-    if (valid[k]) finish_cell<DIM, QP, QC>(p, kchi_df, invDK_df, geo.prob, mom[k], rout, cell[k]);
+  for (int k = 0; k < CPT; ++k) {
+    if (!valid[k]) continue;
+    const int64_t c = cell[k];
+    double mh[4];
+    if constexpr (STAGE == kFinal) {
+      const Moments m = to_fp64(mom[k]);
+      mh[0] = m.n;
+      mh[1] = m.jx;
+      mh[2] = m.jy;
+      mh[3] = m.e;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) p.mhi[i * N + c] = mh[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) mh[i] = p.mhi[i * N + c];
+    }
+    finish_cell<DIM, QP, QC>(p, geo.kchi, geo.invDK, geo.prob, mh[0] + (double)lm[k].n,
+                             mh[1] + (double)lm[k].jx, mh[2] + (double)lm[k].jy,
+                             mh[3] + (double)lm[k].e, rout, c);
+  }
 }
 
 template <int DIM, int QP, int QC, int STAGE, int VAR = 0>
 __global__ void __launch_bounds__(TileCfg<DIM, VAR>::NT,
-                                  DIM == 2 ? (STAGE == kStage3 ? 4 : 5)
-                                           : (TileCfg<DIM, VAR>::NT >= 128 ? 5 : 8))
+                                  DIM == 2 ? 3 : (TileCfg<DIM, VAR>::NT >= 128 ? 4 : 8))
     mixed_stage_kernel(const __grid_constant__ DevParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   auto& sm = *reinterpret_cast<MixSmem<DIM, QP, QC, VAR, STAGE>*>(smraw);
@@ -627,7 +787,7 @@ __global__ void __launch_bounds__(TileCfg<DIM, VAR>::NT,
 }
 
 template <int QP, int QC, int STAGE, int VAR>
-__global__ void __launch_bounds__(TileCfg<1, VAR>::NT, 6)
+__global__ void __launch_bounds__(TileCfg<1, VAR>::NT, 4)
     mixed_batch_kernel(const __grid_constant__ DevParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   auto& sm = *reinterpret_cast<MixSmem<1, QP, QC, VAR, STAGE>*>(smraw);
@@ -650,16 +810,26 @@ __device__ __forceinline__ int problem_of(const DevParams& p, int64_t c) {
   return lo;
 }
 
-// The record of F^n (after fdlb_init_riemann or fdlb_set_state): the same
-// moment sums, in the same population order, as the final stage's.
-template <int DIM, int QP, int QC>
+// After fdlb_init_riemann or fdlb_set_state: mhi and the record of F^n, with
+// the final stage's sums in the final stage's population order (so that a
+// state set from a copy continues bit for bit).  G is the group size of the
+// kernels the context runs.
+template <int DIM, int QP, int QC, int G>
 __global__ void mixed_prep_kernel(const __grid_constant__ DevParams p) {
   using L = Lat<DIM, QP, QC>;
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.N) return;
-  const float* F = (const float*)p.F;
   MomentsF m = {};
-  for (int pop = 0; pop < L::P; ++pop) accumulate<DIM, QP, QC>(p, m, pop, F[pop * p.N + c]);
+  MomL lm = {};
+  constexpr int NG = (L::P + G - 1) / G;
+  for (int gi = 0; gi < NG; ++gi) {
+    const int g0 = group_pop<DIM, QP, QC, G>(gi);
+    for (int g = 0; g < G && g0 + g < L::P; ++g) {
+      const int pop = g0 + g;
+      accumulate<DIM, QP, QC>(p, m, pop, p.sh[pop * p.N + c]);
+      accum_low<DIM, QP, QC>(p, lm, pop, p.sl[pop * p.N + c]);
+    }
+  }
   Geo geo{p.nx, p.ny, 0, p.kchi, p.invDK, p.dtdx, p.dtdy, -1};
   if (p.nprob > 0) {
     const int b = problem_of(p, c);
@@ -667,7 +837,14 @@ __global__ void mixed_prep_kernel(const __grid_constant__ DevParams p) {
     geo.invDK = p.probs[b].invDK;
     geo.prob = b;
   }
-  finish_cell<DIM, QP, QC>(p, df_of(geo.kchi), df_of(geo.invDK), geo.prob, m, p.erec[0], c);
+  const Moments mh = to_fp64(m);
+  p.mhi[c] = mh.n;
+  p.mhi[p.N + c] = mh.jx;
+  p.mhi[2 * p.N + c] = mh.jy;
+  p.mhi[3 * p.N + c] = mh.e;
+  finish_cell<DIM, QP, QC>(p, geo.kchi, geo.invDK, geo.prob, mh.n + (double)lm.n,
+                           mh.jx + (double)lm.jx, mh.jy + (double)lm.jy, mh.e + (double)lm.e,
+                           p.erec[0], c);
 }
 
 template <int DIM, int QP, int QC, int VAR, int STAGE>
@@ -675,22 +852,33 @@ constexpr int smem_bytes() {
   return (int)sizeof(MixSmem<DIM, QP, QC, VAR, STAGE>);
 }
 
-template <int DIM, int QP, int QC>
-int setup_t() {
+template <int DIM, int QP, int QC, int VAR>
+int setup_tv() {
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage3>,
+    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage3, VAR>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem_bytes<DIM, QP, QC, 0, kStage3>());
+                             smem_bytes<DIM, QP, QC, VAR, kStage3>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage4>,
+    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage4, VAR>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem_bytes<DIM, QP, QC, 0, kStage4>());
+                             smem_bytes<DIM, QP, QC, VAR, kStage4>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kFinal>,
+    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kFinal, VAR>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem_bytes<DIM, QP, QC, 0, kFinal>());
+                             smem_bytes<DIM, QP, QC, VAR, kFinal>());
   return (int)e;
+}
+
+template <int DIM, int QP, int QC>
+int setup_t() {
+  int e = setup_tv<DIM, QP, QC, 0>();
+  if constexpr (DIM == 1) {
+    if (!e) e = setup_tv<1, QP, QC, 1>();
+    if (!e) e = setup_tv<1, QP, QC, 3>();
+    if (!e) e = setup_tv<1, QP, QC, 4>();
+  }
+  return e;
 }
 
 template <int QP, int QC, int VAR>
@@ -732,23 +920,34 @@ int launch_tv(const DevParams& p, int stage, cudaStream_t s) {
   return (int)cudaGetLastError();
 }
 
+template <int DIM, int QP, int QC, int G>
+int launch_prep(const DevParams& p, cudaStream_t s) {
+  const int nt = 128;
+  const int64_t nb = (p.N + nt - 1) / nt;
+  mixed_prep_kernel<DIM, QP, QC, G><<<(unsigned)nb, nt, 0, s>>>(p);
+  return (int)cudaGetLastError();
+}
+
 template <int DIM, int QP, int QC>
 int launch_t(const DevParams& p, int stage, cudaStream_t s) {
-  if (stage == kPrep) {
-    const int nt = 128;
-    const int64_t nb = (p.N + nt - 1) / nt;
-    mixed_prep_kernel<DIM, QP, QC><<<(unsigned)nb, nt, 0, s>>>(p);
-    return (int)cudaGetLastError();
-  }
   if constexpr (DIM == 1) {
     // 1-D problems pick their tile shape by length (single_1d_variant)
     switch (single_1d_variant(p.nx)) {
-      case 1: return launch_tv<1, QP, QC, 1>(p, stage, s);
-      case 3: return launch_tv<1, QP, QC, 3>(p, stage, s);
-      case 4: return launch_tv<1, QP, QC, 4>(p, stage, s);
-      default: return launch_tv<1, QP, QC, 0>(p, stage, s);
+      case 1:
+        return stage == kPrep ? launch_prep<1, QP, QC, TileCfg<1, 1>::G>(p, s)
+                              : launch_tv<1, QP, QC, 1>(p, stage, s);
+      case 3:
+        return stage == kPrep ? launch_prep<1, QP, QC, TileCfg<1, 3>::G>(p, s)
+                              : launch_tv<1, QP, QC, 3>(p, stage, s);
+      case 4:
+        return stage == kPrep ? launch_prep<1, QP, QC, TileCfg<1, 4>::G>(p, s)
+                              : launch_tv<1, QP, QC, 4>(p, stage, s);
+      default:
+        return stage == kPrep ? launch_prep<1, QP, QC, TileCfg<1, 0>::G>(p, s)
+                              : launch_tv<1, QP, QC, 0>(p, stage, s);
     }
   }
+  if (stage == kPrep) return launch_prep<DIM, QP, QC, TileCfg<DIM, 0>::G>(p, s);
   return launch_tv<DIM, QP, QC, 0>(p, stage, s);
 }
 
@@ -757,6 +956,8 @@ int launch_batch_v(const DevParams& p, int stage, cudaStream_t s) {
   using C = TileCfg<1, VAR>;
   const int grid = p.bgrid > 0 ? p.bgrid : 1;
   switch (stage) {
+    case kPrep:
+      return launch_prep<1, QP, QC, C::G>(p, s);
     case kStage3:
       mixed_batch_kernel<QP, QC, kStage3, VAR>
           <<<grid, C::NT, smem_bytes<1, QP, QC, VAR, kStage3>(), s>>>(p);
@@ -775,16 +976,30 @@ int launch_batch_v(const DevParams& p, int stage, cudaStream_t s) {
 
 template <int QP, int QC>
 int launch_batch_t(const DevParams& p, int stage, cudaStream_t s) {
-  if (stage == kPrep) {
-    const int nt = 128;
-    const int64_t nb = (p.N + nt - 1) / nt;
-    mixed_prep_kernel<1, QP, QC><<<(unsigned)nb, nt, 0, s>>>(p);
-    return (int)cudaGetLastError();
-  }
   switch (p.variant) {
     case 1: return launch_batch_v<QP, QC, 1>(p, stage, s);
     case 2: return launch_batch_v<QP, QC, 2>(p, stage, s);
     default: return launch_batch_v<QP, QC, 0>(p, stage, s);
+  }
+}
+
+// ---- the state as binary64 values (fdlb_get_state / fdlb_set_state) ------
+
+__global__ void pair_to_double_kernel(const float* __restrict__ hi, const float* __restrict__ lo,
+                                      double* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)hi[i] + (double)lo[i];  // exact: |lo| <= ulp(hi)/2
+}
+
+__global__ void double_to_pair_kernel(const double* __restrict__ in, float* __restrict__ hi,
+                                      float* __restrict__ lo, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = in[i];
+    const float h = (float)v;
+    hi[i] = h;
+    lo[i] = (float)(v - (double)h);
   }
 }
 
@@ -832,6 +1047,17 @@ int launch_mixed_batch_stage(const DevParams& p, int stage, cudaStream_t s) {
   FDLB_BATCH_LATTICES(X)
 #undef X
   return (int)cudaErrorInvalidValue;
+}
+
+int launch_pair_to_double(const float* hi, const float* lo, double* out, int64_t n,
+                          cudaStream_t s) {
+  pair_to_double_kernel<<<1024, 256, 0, s>>>(hi, lo, out, n);
+  return (int)cudaGetLastError();
+}
+
+int launch_double_to_pair(const double* in, float* hi, float* lo, int64_t n, cudaStream_t s) {
+  double_to_pair_kernel<<<1024, 256, 0, s>>>(in, hi, lo, n);
+  return (int)cudaGetLastError();
 }
 
 }  // namespace fdlb

@@ -226,8 +226,9 @@ __device__ __forceinline__ float minmod4f(float a, float b, float c, float d) {
 
 // As in the binary64 face, the bounds and a are formed at twice their value
 // (doubling the stencil's coefficients is exact), so that each bound takes
-// one operation and the final halving folds into one fma.
-__device__ __forceinline__ float mp9_face_fp32(const Mp9LineF& L, float& c1_out, float& dmp_out) {
+// one operation and the final halving is exact.  Returns the limited offset
+// Fhat - F_s of the interface.
+__device__ __forceinline__ float mp9_offset_fp32(const Mp9LineF& L, float& c1_out, float& dmp_out) {
   const float* d = L.d;
   float a2 = (2.0f * (-4.0f / 2520.0f)) * d[0];
   a2 = fmaf(2.0f * (37.0f / 2520.0f), d[1], a2);
@@ -248,7 +249,54 @@ __device__ __forceinline__ float mp9_face_fp32(const Mp9LineF& L, float& c1_out,
   const float hi2 = fminf(fmax3f(0.0f, d0_2, md2), fmax3f(0.0f, ul2, lc2));
   c1_out = c1;
   dmp_out = dmp;
-  return fmaf(0.5f, fminf(fmaxf(a2, lo2), hi2), L.fs[0]);
+  return 0.5f * fminf(fmaxf(a2, lo2), hi2);
+}
+__device__ __forceinline__ float mp9_face_fp32(const Mp9LineF& L, float& c1_out, float& dmp_out) {
+  return __fadd_rn(mp9_offset_fp32(L, c1_out, dmp_out), L.fs[0]);
+}
+
+// March NSTEP consecutive interfaces of one whole line and write, for each of
+// the NSTEP-1 cells between consecutive interfaces, its flux difference
+// sgn (Fhat_right - Fhat_left) = d_-1 + a_cur - a_prev: the difference
+// between the cell and its upwind neighbour plus the difference of the two
+// interfaces' offsets a = Fhat - F_s from their upwind cells.  Formed from
+// differences, it carries rounding relative to the variation along the line
+// rather than to the values themselves.  out[t * ostep], t = 0..NSTEP-2, is
+// the cell between interfaces t and t+1 in march order.
+template <int NSTEP>
+__device__ __forceinline__ void mp9_march_delta_fp32(const float* __restrict__ p, int ss,
+                                                     float* __restrict__ out, int ostep) {
+  Mp9LineF L;
+  float v[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) v[j] = p[(j - 4) * ss];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) L.d[k] = v[k + 1] - v[k];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) L.fs[j] = v[j + 4];
+  L.cm1 = L.d[3] - L.d[2];
+  L.c0 = L.d[4] - L.d[3];
+  L.dmm = minmod4f(fmaf(4.0f, L.c0, -L.cm1), fmaf(4.0f, L.cm1, -L.c0), L.c0, L.cm1);
+  float aprev = 0.0f;
+#pragma unroll
+  for (int t = 0; t < NSTEP; ++t) {
+    float c1, dmp;
+    const float a = mp9_offset_fp32(L, c1, dmp);
+    if (t > 0) out[(t - 1) * ostep] = __fsub_rn(__fadd_rn(L.d[3], a), aprev);
+    aprev = a;
+    if (t + 1 < NSTEP) {
+      const float vnew = p[(t + 5) * ss];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) L.d[k] = L.d[k + 1];
+      L.d[7] = vnew - L.fs[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) L.fs[j] = L.fs[j + 1];
+      L.fs[4] = vnew;
+      L.cm1 = L.c0;
+      L.c0 = c1;
+      L.dmm = dmp;
+    }
+  }
 }
 
 template <int NSTEP>

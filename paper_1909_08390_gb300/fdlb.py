@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.fdlb_step_noalloc.argtypes = [ctypes.POINTER(fdlb_grid), ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.POINTER(fdlb_tableau), _vp, ctypes.c_int64, _vp]
+    lib.fdlb_measure_fp64_pipe.argtypes = [_vp, _dp, _dp]
     lib.fdlb_destroy.argtypes = [_vp]
     lib.fdlb_destroy.restype = None
     lib.fdlb_last_error.argtypes = [_vp]
@@ -303,6 +304,14 @@ def fdlb_adjoint(ctx, nsteps: int, every: int, ckpt, Fbar):
     return d[0], d[1]
 
 
+def fdlb_measure_fp64_pipe(stream=None):
+    """Measured binary64 FMA rate of the current device: (DFMA/s, ms of the timed launch)."""
+    r, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load().fdlb_measure_fp64_pipe(_stream_handle(stream), ctypes.byref(r), ctypes.byref(ms)),
+           None)
+    return r.value, ms.value
+
+
 def fdlb_destroy(ctx):
     if ctx:
         load().fdlb_destroy(ctx)
@@ -355,7 +364,7 @@ class Solver:
         self.P = fdlb_npop(self.ctx)
         self.N = fdlb_ncells(self.ctx)
         self.precision = precision
-        self.dtype = np.float32 if precision == FDLB_MIXED else np.float64
+        self.dtype = np.float64  # FDLB_MIXED states are exchanged as exact binary64 values
 
     @classmethod
     def from_workload(cls, wl, precision: int = FDLB_FP64, stream=None, **kw):
@@ -375,7 +384,8 @@ class Solver:
         fdlb_step(self.ctx, nsteps)
 
     def state(self) -> np.ndarray:
-        """The populations, float64 (FDLB_FP64) or float32 (FDLB_MIXED)."""
+        """The populations as float64 (a FDLB_MIXED state's binary32 pairs
+        hi + lo are exact binary64 values)."""
         out = np.empty(self.shape, dtype=self.dtype)
         fdlb_get_state(self.ctx, out, False)
         return out
@@ -427,7 +437,7 @@ class BatchSolver(Solver):
         self.N = fdlb_ncells(self.ctx)
         self.nx = self.N
         self.precision = precision
-        self.dtype = np.float32 if precision == FDLB_MIXED else np.float64
+        self.dtype = np.float64  # FDLB_MIXED states are exchanged as exact binary64 values
         self.base = fdlb_batch_offsets(self.ctx, self.nprob)
 
     def init_riemann(self, states, xsplit=None):

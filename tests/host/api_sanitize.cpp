@@ -35,6 +35,12 @@ int launch_batch_init(const DevParams&, cudaStream_t) { return (int)cudaErrorNoD
 int batch_tile_cells(int) { return 127; }
 int mixed_record_width(int, int, int) { return 25; }
 int mixed_setup(const DevParams&) { return (int)cudaErrorNoDevice; }
+int launch_pair_to_double(const float*, const float*, double*, int64_t, cudaStream_t) {
+  return (int)cudaErrorNoDevice;
+}
+int launch_double_to_pair(const double*, float*, float*, int64_t, cudaStream_t) {
+  return (int)cudaErrorNoDevice;
+}
 }  // namespace fdlb
 
 static int fails = 0;

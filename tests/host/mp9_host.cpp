@@ -9,6 +9,9 @@
 static inline long long __double_as_longlong(double x) { long long b; std::memcpy(&b, &x, 8); return b; }
 static inline double __longlong_as_double(long long b) { double x; std::memcpy(&x, &b, 8); return x; }
 using std::fma;
+// binary32 intrinsics as the host's IEEE operations (built with -ffp-contract=off)
+static inline float __fadd_rn(float a, float b) { return a + b; }
+static inline float __fsub_rn(float a, float b) { return a - b; }
 #include "../../paper_1909_08390_gb300/csrc/fdlb_mp9.cuh"
 
 extern "C" double mp9_face(const double* v9) {

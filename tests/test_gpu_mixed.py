@@ -1,13 +1,13 @@
-"""Mixed precision (binary32 populations, binary64-accurate moments,
-temperature and relaxation coefficients) against the binary64 CPU oracle and
-the binary64 GPU path, through the C ABI.
+"""Mixed precision against the binary64 CPU oracle and the binary64 GPU path,
+through the C ABI.  The mixed path keeps each population as a pair of
+binary32 values, the stages' explicit parts as binary32 increments on it,
+advects and relaxes in binary32, and recovers n, u and T (the cancellation
+in T = (E - n u^2)/((D+K) n) included) in binary64 per cell.
 
 Bar: 1e-5 relative (||.||_inf / ||.||_inf) in n, u (normalised by
-max(|u|, 1)) and T, and in the populations.  Storage rounds every population
-to 24 bits (6e-8 relative) at each of the four stages; the MP-9/limiter
-arithmetic and the relaxation run in binary32; the moments are summed with
-error-free binary32 transformations and folded into binary64, so the
-cancellation in T = (E - n u^2)/((D+K) n) is not amplified.
+max(|u|, 1)) and T, and in the populations, for every run length the
+workloads state: the 1-D shock tube to t = 0.1 (2000 steps), the 512^2
+benchmark problem and the 2048^2 problem to 2000 steps.
 """
 import numpy as np
 import pytest
@@ -42,13 +42,8 @@ def fields_err(got, want):
 
 def test_mixed_sod_1d_against_oracle(oracle, F):
     """1-D Sod (Nx = 400, Q = 8, gamma = 7/5, tau = 1e-6, dt = 5e-5): after
-    1000 steps every field and the populations are within 1e-5 of the oracle;
-    at t = 0.1 (2000 steps) n, T and the populations are.  The velocity at
-    t = 0.1 gets 2e-5: its largest difference sits in the shock cell, where
-    the binary32 rounding of every stored population (6e-8 relative, four
-    stages per step) accumulates to about 1e-5 whatever the record arithmetic
-    (measured between 9.1e-6 and 1.0e-5 across the binary64 and pair
-    evaluations of the records; 2.8e-6 at 1000 steps)."""
+    1000 steps and at t = 0.1 (2000 steps) every field and the populations
+    are within 1e-5 of the oracle."""
     wl = W.sod_1d()
     pr = oracle.Problem(d=1, nx=wl.nx, x0=wl.x0, x1=wl.x1, Qphi=8, Qchi=8, gamma=wl.gamma,
                         tau=wl.tau, dt=wl.dt)
@@ -59,12 +54,11 @@ def test_mixed_sod_1d_against_oracle(oracle, F):
             s.init_riemann(wl.states, wl.xsplit)
             s.step(nsteps)
             G = s.state()
-            assert G.dtype == np.float32
+            assert G.dtype == np.float64
             err = fields_err(s.moments(), oracle.moments(pr, want))
         print(f"mixed Sod, {nsteps} steps:", err)
-        tol_u = TOL if nsteps < wl.nsteps else 2e-5
-        assert err["n"] < TOL and err["T"] < TOL and err["u"] < tol_u, err
-        assert rel(G.astype(np.float64), want) < TOL
+        assert max(err.values()) < TOL, err
+        assert rel(G, want) < TOL
 
 
 @pytest.mark.parametrize("Q", [(8, 8), (5, 3)])
@@ -116,18 +110,22 @@ def test_mixed_conservation_periodic(F):
 
 def test_mixed_2048_against_fp64_gpu(F):
     """2048 x 2048 cells x 128 populations (2.1 GB per binary32 array) with the
-    benchmark seed's quadrant states, dt = 2.5e-5, tau = 1e-6: the mixed and
-    binary64 GPU runs agree to 1e-5 in n, u, v, T after 200 steps."""
+    benchmark seed's quadrant states, dt = 2.5e-5, tau = 1e-6, for the 2000
+    steps of that workload: the mixed and binary64 GPU runs agree to 1e-5 in
+    n, u, v, T in the max norm (checked also after 200 steps)."""
     wl = W.quadrant_2d(W.BENCH_SEED, n=2048)
     out = {}
     for prec in (F.FDLB_FP64, F.FDLB_MIXED):
         with F.Solver.from_workload(wl, precision=prec) as s:
             s.init_riemann(wl.states, 0.5, 0.5)
             s.step(200)
-            out[prec] = s.moments()
-    err = fields_err(out[F.FDLB_MIXED], out[F.FDLB_FP64])
-    print("2048^2, 200 steps, mixed vs binary64:", err)
-    assert max(err.values()) < TOL, err
+            first = s.moments()
+            s.step(1800)
+            out[prec] = (first, s.moments())
+    for i, steps in enumerate((200, 2000)):
+        err = fields_err(out[F.FDLB_MIXED][i], out[F.FDLB_FP64][i])
+        print(f"2048^2, {steps} steps, mixed vs binary64:", err)
+        assert max(err.values()) < TOL, (steps, err)
 
 
 def test_benchmark_seed_on_256_grid_against_oracle(F, oracle):
@@ -149,12 +147,8 @@ def test_benchmark_seed_on_256_grid_against_oracle(F, oracle):
 
 
 def test_mixed_512_long_run_against_fp64_gpu(F):
-    """2000 steps of the benchmark problem (512 x 512 x 128): the binary32
-    storage rounding accumulates step by step (a binary64 run started from
-    the binary32-rounded state stays within 6e-8 of the binary64 run, so the
-    problem itself does not amplify a one-time rounding), reaching 0.6-1.5e-6
-    in relative L1 and 1.4-3.1e-5 in the max norm, where it sits in the
-    discontinuities.  Bars: 1e-5 in L1, 1e-4 in the max norm."""
+    """2000 steps of the benchmark problem (512 x 512 x 128): mixed against
+    binary64 within 1e-5 in the max norm and in relative L1 for n, u, v, T."""
     wl = W.quadrant_2d(W.BENCH_SEED)
     out = {}
     for prec in (F.FDLB_FP64, F.FDLB_MIXED):
@@ -166,4 +160,4 @@ def test_mixed_512_long_run_against_fp64_gpu(F):
         l1 = np.abs(a - b).sum() / max(np.abs(b).sum(), floor * b.size)
         mx = np.abs(a - b).max() / max(np.abs(b).max(), floor)
         print(f"512^2, 2000 steps, {name}: L1 {l1:.2e}, max {mx:.2e}")
-        assert l1 < TOL and mx < 1e-4, (name, l1, mx)
+        assert l1 < TOL and mx < TOL, (name, l1, mx)
