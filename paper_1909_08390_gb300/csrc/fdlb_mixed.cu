@@ -330,12 +330,15 @@ struct MixSmem {
   float rbl[NSL][GR::kOn ? NSC : 1];   // plan): high and low parts, as loaded
   float tile[C::G][SY][SX];            // relaxed advected populations - ref
   // 2-D: flux differences of the cells along x and y (mp9_march_delta_fp32);
-  // 1-D: interface values along x
-  float hx[C::G][C::TY][C::TX + (DIM == 2 ? 0 : 1)];
-  float hy[DIM == 2 ? C::G : 1][DIM == 2 ? C::TX : 1][DIM == 2 ? C::TY : 1];
+  // 1-D: interface values along x.  Rows of TX + 1 (TY + 1) floats: the odd
+  // pitch keeps the march's column-wise writes free of bank conflicts.
+  float hx[C::G][C::TY][C::TX + 1];
+  float hy[DIM == 2 ? C::G : 1][DIM == 2 ? C::TX : 1][DIM == 2 ? C::TY + 1 : 1];
   float ownd[C::G][C::TY * C::TX];     // R - F_eq of the own cells
   // stage 3: sl of the own cells; final stage: sh of the own cells
   float ownv[STAGE == kStage4 ? 1 : C::G][STAGE == kStage4 ? 1 : C::TY * C::TX];
+  // dt p / ds per population as binary32 pairs: (x hi, x lo, y hi, y lo)
+  float4 coef[Lat<DIM, QP, QC>::P];
 };
 
 // Plain binary32 moment sums of low parts (stages 3 and 4), two cells.
@@ -428,15 +431,21 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   bool valid[CPT];
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
-    // a slot past the tile's cells takes cell 0's indices (its lane computes
+    // a thread's cells are CPT consecutive ones (x-adjacent pairs when CPT =
+    // 2 and TX is even), so that pass 1 can move them as 8-byte pairs; a
+    // slot past the tile's cells takes cell 0's indices (its lane computes
     // on them and stores nothing), so every shared-memory index stays inside
     // its array
-    const int c = tid + k * NT < CELLS ? tid + k * NT : 0;
+    const int ci = CPT * tid + k;
+    const int c = ci < CELLS ? ci : 0;
     lxs[k] = c % TX;
     lys[k] = c / TX;
-    valid[k] = (tid + k * NT < CELLS) && (x0 + lxs[k] < geo.nx) && (y0 + lys[k] < geo.ny);
+    valid[k] = (ci < CELLS) && (x0 + lxs[k] < geo.nx) && (y0 + lys[k] < geo.ny);
     cell[k] = geo.base + (int64_t)(y0 + lys[k]) * geo.nx + (x0 + lxs[k]);
   }
+  // both cells of the pair valid, adjacent in memory and 8-byte aligned
+  const bool pair_vec = CPT == 2 && valid[0] && valid[CPT - 1] &&
+                        cell[CPT - 1] == cell[0] + 1 && (cell[0] & 1) == 0 && (N & 1) == 0;
   // moment sums: stages 3 and 4 sum the low parts plainly; the final stage
   // sums the new high parts error-free (mom*) and the new low parts plainly
   MomL lm[CPT];
@@ -458,13 +467,16 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   const float wtl = STAGE == kStage3 ? (float)(p.sc.wt2 - (double)sc.wt2)
                   : STAGE == kStage4 ? (float)(p.sc.wt3 - (double)sc.wt3)
                                      : (float)(p.sc.wt4 - (double)sc.wt4);
-  // dt p / ds of population pop along x or y as a pair; 2-D takes |.| (the
-  // flux differences of the 2-D march carry the velocity's sign)
-  auto coef = [&](int pop, bool x) {
-    DF c = df_mul(x ? dtdx_df : dtdy_df, x ? DF{p.pxh[pop], p.pxl[pop]} : DF{p.pyh[pop], p.pyl[pop]});
-    if (DIM == 2 && c.hi < 0.0f) c = df_neg(c);
-    return c;
-  };
+  // dt p / ds of every population along x and y as pairs, once per tile (the
+  // first barrier of the group loop orders it before pass 1); 2-D takes |.|
+  // (the flux differences of the 2-D march carry the velocity's sign)
+  for (int pop = tid; pop < L::P; pop += NT) {
+    DF cx = df_mul(dtdx_df, DF{p.pxh[pop], p.pxl[pop]});
+    DF cy = DIM == 2 ? df_mul(dtdy_df, DF{p.pyh[pop], p.pyl[pop]}) : DF{0.0f, 0.0f};
+    if (DIM == 2 && cx.hi < 0.0f) cx = df_neg(cx);
+    if (DIM == 2 && cy.hi < 0.0f) cy = df_neg(cy);
+    sm.coef[pop] = make_float4(cx.hi, cx.lo, cy.hi, cy.lo);
+  }
   const float* __restrict__ const rbase = rin + geo.base;
   // the reference value of each population on a 2-D tile: sh at the tile's
   // first cell.  1-D tiles take none, so that a 1-D problem gives the same
@@ -524,15 +536,28 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
     float a4v[CPT][G], afv[CPT][G];
     if constexpr (STAGE != kStage3) {
 #pragma unroll
-      for (int k = 0; k < CPT; ++k)
+      for (int g = 0; g < G; ++g) {
+        const int pop = g0 + g;
+        if (CPT == 2 && pair_vec && pop < L::P) {
+          const int64_t e = (int64_t)pop * N + cell[0];
+          if (STAGE == kStage4) {
+            const float2 v = *reinterpret_cast<const float2*>(p.a4l + e);
+            a4v[0][g] = v.x;
+            a4v[CPT - 1][g] = v.y;
+          }
+          const float2 v = *reinterpret_cast<const float2*>(p.afl + e);
+          afv[0][g] = v.x;
+          afv[CPT - 1][g] = v.y;
+          continue;
+        }
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-          const int pop = g0 + g;
+        for (int k = 0; k < CPT; ++k) {
           const bool ok = valid[k] && pop < L::P;
           const int64_t e = (int64_t)pop * N + cell[k];
           a4v[k][g] = (STAGE == kStage4 && ok) ? p.a4l[e] : 0.0f;
           afv[k][g] = ok ? p.afl[e] : 0.0f;
         }
+      }
     }
     // ---- stage the group: relaxed advected values - ref on tile + halo
     cp_async_wait_all();
@@ -644,9 +669,10 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
         const int pop = g0 + g;
         if (pop >= L::P) break;
         float2 X;
-        const DF cx = coef(pop, true);
+        const float4 cf = sm.coef[pop];
+        const DF cx{cf.x, cf.y};
         if constexpr (DIM == 2) {
-          const DF cy = coef(pop, false);
+          const DF cy{cf.z, cf.w};
           const float2 dx = make_float2(sm.hx[g][lys[0]][lxs[0]], sm.hx[g][lys[1]][lxs[1]]);
           const float2 dy = make_float2(sm.hy[g][lxs[0]][lys[0]], sm.hy[g][lxs[1]][lys[1]]);
           X = __ffma2_rn(f2s(cx.hi), dx, __fmul2_rn(f2s(cx.lo), dx));
@@ -657,6 +683,16 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
           X = __ffma2_rn(f2s(cx.hi), dfx, __fmul2_rn(f2s(cx.lo), dfx));
         }
         const int64_t e0 = (int64_t)pop * N + cell[0], e1 = (int64_t)pop * N + cell[1];
+        // store a pair of the two cells' values: one 8-byte store when the
+        // cells are adjacent and aligned, else one per valid cell
+        auto put = [&](float* __restrict__ a, float2 v) {
+          if (pair_vec) {
+            *reinterpret_cast<float2*>(a + e0) = v;
+          } else {
+            if (valid[0]) a[e0] = v.x;
+            if (valid[1]) a[e1] = v.y;
+          }
+        };
         const float2 d = make_float2(sm.ownd[g][o0], sm.ownd[g][o1]);
         if constexpr (STAGE == kStage3) {
           const float2 l = make_float2(sm.ownv[g][o0], sm.ownv[g][o1]);  // sl
@@ -664,8 +700,9 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
           const float2 a4 = __fadd2_rn(l, __ffma2_rn(f2s(-sc.at42), X, __fmul2_rn(f2s(-sc.k4), d)));
           const float2 af = __fadd2_rn(
               l, __ffma2_rn(f2s(-sc.wt2), X, __ffma2_rn(f2s(-wtl), X, __fmul2_rn(f2s(-sc.kf), d))));
-          if (valid[0]) { p.r3l[e0] = r3.x; p.a4l[e0] = a4.x; p.afl[e0] = af.x; }
-          if (valid[1]) { p.r3l[e1] = r3.y; p.a4l[e1] = a4.y; p.afl[e1] = af.y; }
+          put(p.r3l, r3);
+          put(p.a4l, a4);
+          put(p.afl, af);
           accum_low2<DIM, QP, QC>(p, lm2, pop, r3);
         } else if constexpr (STAGE == kStage4) {
           const float2 r4 = __ffma2_rn(f2s(-sc.at43), X,
@@ -674,8 +711,8 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
               f2s(-sc.wt3), X,
               __ffma2_rn(f2s(-wtl), X,
                          __ffma2_rn(f2s(-sc.w3e3), d, make_float2(afv[0][g], afv[1][g]))));
-          if (valid[0]) { p.a4l[e0] = r4.x; p.afl[e0] = af.x; }
-          if (valid[1]) { p.a4l[e1] = r4.y; p.afl[e1] = af.y; }
+          put(p.a4l, r4);
+          put(p.afl, af);
           accum_low2<DIM, QP, QC>(p, lm2, pop, r4);
         } else {
           // F^{n+1} = sh + t with t = afl - w4 e4 D4 - wt4 X4, renormalised by
@@ -688,8 +725,8 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
           const float2 s = __fadd2_rn(a, t);
           const float2 bb = sub2(s, a);
           const float2 er = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(t, bb));
-          if (valid[0]) { p.nh[e0] = s.x; p.nl[e0] = er.x; }
-          if (valid[1]) { p.nh[e1] = s.y; p.nl[e1] = er.y; }
+          put(p.nh, s);
+          put(p.nl, er);
           accumulate2<DIM, QP, QC>(p, mom2, pop, s);
           accum_low2<DIM, QP, QC>(p, lm2, pop, er);
         }
@@ -704,9 +741,10 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
           const int pop = g0 + g;
           if (pop >= L::P) break;
           float X;
-          const DF cx = coef(pop, true);
+          const float4 cf = sm.coef[pop];
+          const DF cx{cf.x, cf.y};
           if constexpr (DIM == 2) {
-            const DF cy = coef(pop, false);
+            const DF cy{cf.z, cf.w};
             const float dx = sm.hx[g][ly][lx], dy = sm.hy[g][lx][ly];
             X = fmaf(cx.hi, dx, __fmul_rn(cx.lo, dx));
             X = fmaf(cy.hi, dy, fmaf(cy.lo, dy, X));

@@ -84,14 +84,16 @@ def test_batch_config_512_problems_1000_steps(oracle, F):
     Draws whose temperature T = P/rho lies far above the lattice's reference
     temperature leave the range the Q = 8 Hermite-truncated equilibrium
     represents: a mode grows from rounding noise until the state is invalid,
-    in the binary64 oracle as on the GPU.  So:
-    * the binary64 batch flags exactly the members the oracle finds unstable
-      within the 1000 steps: every flagged member fails in the oracle, and a
-      seeded sample of 12 unflagged members stays valid there;
-    * the mixed batch flags every member the binary64 batch flags; its
-      larger rounding seeds the growth sooner, so it may flag more, and each
-      member it alone flags must fail in the binary64 batch within 2000
-      further steps;
+    in the binary64 oracle as on the GPU.  When that happens depends on the
+    rounding, so a member whose growth reaches an invalid state close to step
+    1000 may cross that line earlier, later or not at all with another
+    rounding (measured: the binary64 and mixed batches flag 64 members each
+    with 61 in common; member 207, flagged by the binary64 batch, stays valid
+    in the oracle to step 1000).  So:
+    * every member either batch flags is unstable in the oracle (it fails
+      within 3000 steps), and the two batches agree on all but a few;
+    * a seeded sample of 12 members neither batch flags stays valid in the
+      oracle for the 1000 steps;
     * on the members neither flags: 16 spread over the lengths and gammas
       against the oracle, and every one against the binary64 batch, within
       1e-5 in n, u (normalised by max(|u|, 1)) and T."""
@@ -111,31 +113,37 @@ def test_batch_config_512_problems_1000_steps(oracle, F):
         b64.step(nsteps, allow_unstable=True)
         flags64 = b64.status().copy()
         n64, u64, _, T64 = b64.moments()
-        b64.step(2000, allow_unstable=True)
-        flags64_late = b64.status().copy()
     f32 = {j for j in range(len(nx)) if flags[j]}
     f64 = {j for j in range(len(nx)) if flags64[j]}
-    print(f"flagged after {nsteps} steps: binary64 {len(f64)}, mixed {len(f32)} "
-          f"(mixed only: {sorted(f32 - f64)})")
+    print(f"flagged after {nsteps} steps: binary64 {len(f64)}, mixed {len(f32)}; binary64 only "
+          f"{sorted(f64 - f32)}, mixed only {sorted(f32 - f64)}")
     assert len(f32) < len(nx) // 4
-    assert f64 <= f32, sorted(f64 - f32)
-    for j in sorted(f32 - f64):
-        assert flags64_late[j], f"member {j} flagged by the mixed batch only, stable in binary64"
+    assert len(f32 ^ f64) <= max(4, len(f64) // 10), sorted(f32 ^ f64)
 
-    def oracle_run(j):
+    def oracle_run(j, steps=nsteps):
         pr = oracle.Problem(d=1, nx=nx[j], x0=-0.5, x1=0.5, Qphi=8, Qchi=8, gamma=gm[j],
                             tau=1e-6, dt=2e-5)
         F0 = oracle.init_states(pr, st[j], 0.0)
         try:
-            return pr, oracle.step(pr, F0, nsteps)
+            return pr, oracle.step(pr, F0, steps)
         except oracle.OracleError:
             return pr, None
 
-    for j in sorted(f64):
-        assert oracle_run(j)[1] is None, f"member {j} is flagged but stable in the oracle"
-    stable = [j for j in range(len(nx)) if j not in f32]
+    late = []
+    for j in sorted(f32 | f64):
+        pr, G = oracle_run(j)
+        if G is not None:  # valid at step 1000: it must fail within 2000 more
+            late.append(j)
+            try:
+                oracle.step(pr, G, 2000)
+                ok = True
+            except oracle.OracleError:
+                ok = False
+            assert not ok, f"member {j} is flagged but stable in the oracle to step 3000"
+    print(f"flagged members valid in the oracle at step 1000 (failing later): {late}")
+    stable = [j for j in range(len(nx)) if j not in f32 | f64]
     rng = np.random.default_rng(1000)
-    for j in rng.choice([j for j in range(len(nx)) if j not in f64], size=12, replace=False):
+    for j in rng.choice(stable, size=12, replace=False):
         assert oracle_run(int(j))[1] is not None, f"member {j} unflagged but unstable in the oracle"
     # 16 members neither batch flags, spread over length and gamma
     order = sorted(stable, key=lambda j: (nx[j], gm[j]))
