@@ -58,16 +58,17 @@ FP64_OPS_PER_POP = {"stage3": 30 + 4 + 13, "stage4": 30 + 4 + 11, "final": 30 + 
 # written once each by the kernel (stage 3: F2, F, D -> F3, A4, Af, D3;
 # stage 4: F3, A4, Af, D3 -> F4, Af, D4; final: F4, Af, D4 -> F, D, F2).
 BYTES_PER_POP = {"stage3": 7 * 8, "stage4": 7 * 8, "final": 6 * 8}
-# Mixed precision (single-pass kernels; binary32 arrays, 4 B per population
-# and array): stage 3 reads sh, sl and writes r3l, a4l, afl; stage 4 reads
-# sh, r3l, a4l, afl and writes a4l, afl; the final stage reads sh, a4l, afl and
-# writes the next state's nh, nl.  Per cell and kernel, for the 8x8 lattice:
-# the equilibrium record read (24 binary32-pair components: A, B and C B) and
-# written (25, C too), and the binary64 moment sums of sh (4 doubles) read by
-# stages 3 and 4 and written by the final stage.
-MIXED_CELL_BYTES_PER_POP = ((24 + 25) * 8 + 4 * 8) / 128
+# Mixed precision (binary32 arrays, 4 B per population and array; each array
+# a kernel touches counted once): stage 3 reads sh, fa, D, sl and writes r3l,
+# a4l, afl, D, fb; stage 4 reads sh, fb, D, a4l, afl and writes a4l, afl, D,
+# fc; the final stage reads sh, fc, D, afl and writes the next state's nh, nl,
+# D, fa.  (Each kernel's second, per-cell pass re-reads two arrays it has
+# just read or written; those re-reads are not counted.)  Per cell: the
+# binary64 moment sums of sh (4 doubles), read by stages 3 and 4 and written
+# by the final stage: 32 / 128 B per population for the 8x8 lattice.
+MIXED_CELL_BYTES_PER_POP = 4 * 8 / 128
 BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_CELL_BYTES_PER_POP
-                       for k, n in (("stage3", 5), ("stage4", 6), ("final", 5))}
+                       for k, n in (("stage3", 9), ("stage4", 9), ("final", 8))}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # ncu captures of the stage kernels on this workload, valid for the kernel sources
 # whose SHA-256 (over STAGE_KERNEL_SOURCES in that order, comments removed) is
@@ -534,9 +535,12 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         b_ms = _max_over_ranks(world, b0.elapsed_time(b1))
         b_units = bs.P * total_cells * args.steps  # all ranks' problems
-        b_gbs = ((64 + 3 * (2 * 9 * 8 + 4 * 8) / 16) * bs.P * total_cells / world
+        b_gbs = ((4 * 26 + 3 * 4 * 8 / 16) * bs.P * total_cells / world
                  / (b_ms / args.steps * 1e-3) / 1e9)
         flags = bs.status()
+        # cells of the members that stayed valid (all ranks): the unstable
+        # members' cells are stepped too, but their results are not valid
+        stable_cells = _sum_over_ranks(world, float(sum(n for n, f in zip(bnx, flags) if f == 0)))
         bs.close()
         # sequential binary64 single-problem contexts on every 16th problem
         # (one GPU only: the comparison is with the batch on the same GPU)
@@ -566,7 +570,9 @@ def run_ours(args, world, rank, local):
                         "U[1.1,5/3], Q=8 (16 populations), tau=1e-6, dt=2e-5" % total_cells,
             "scaling": "strong (the 512 problems dealt out over the ranks)",
             "problems_per_rank": len(probs),
-            "value": b_units / (b_ms * 1e-3), "unit": UNIT,
+            "value": bs.P * stable_cells * args.steps / (b_ms * 1e-3), "unit": UNIT,
+            "value_scope": "updates of the members that stayed valid",
+            "value_all_members": b_units / (b_ms * 1e-3),
             "dtype": "f32 storage/advection, f64-accurate moments",
             "ms_per_step": b_ms / args.steps,
             "sequential_fp64_ms_per_step": seq_ms_all / args.steps if seq_ms_all else None,
@@ -574,10 +580,10 @@ def run_ours(args, world, rank, local):
             "sequential_sample": "every 16th problem (32), scaled by cell count",
             "tiling": {"cells_per_tile": [127, 63, 255][variant], "ctas_per_sm": ctas},
             "unstable_members": int(_sum_over_ranks(world, float((flags != 0).sum()))),
-            # whole-step algorithmic HBM bytes of the three single-pass kernels:
-            # 16 population-array accesses of 4 B and, per kernel and cell, one
-            # 9-component record of binary32 pairs read and one written and the
-            # 4 binary64 moment sums ((2 * 9 * 8 + 32) / 16 B per population)
+            # whole-step algorithmic HBM bytes of the three kernels: 26
+            # population-array accesses of 4 B (each array a kernel touches,
+            # once) and, per kernel and cell, the 4 binary64 moment sums of sh
+            # (32 / 16 B per population)
             "roofline": {
                 "bound": "hbm", "scope": "whole step (3 kernels), per GPU",
                 "achieved": b_gbs, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",

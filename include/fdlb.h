@@ -26,7 +26,10 @@
  *   populations 0 .. Qphi^d-1 are phi_k, k = ky*Qphi + kx (1-D: kx);
  *   populations Qphi^d .. P-1 are chi_q, q = qy*Qchi + qx;
  *   momenta in ascending order along each axis.
- * Element type: double for FDLB_FP64 contexts, float for FDLB_MIXED contexts.
+ * Element type: double for both precisions.  An FDLB_MIXED context keeps
+ * each population as an unevaluated sum of two binary32 numbers (high part
+ * and the rounding residual below it) and converts to and from binary64 at
+ * fdlb_get_state / fdlb_set_state.
  *
  * Ownership: the context owns every device buffer it allocates (cudaMalloc in
  * fdlb_create, freed by fdlb_destroy).  Callers own the arrays they pass in;
@@ -111,11 +114,14 @@ int fdlb_named_tableau(int which, fdlb_tableau* out);
  *                dt max|p| / dx <= 1 on every axis (Sec. IV CFL condition)
  *   tableau    : NULL for IMEX-SSP3(4,3,3) of Table I
  *   precision  : FDLB_FP64: populations stored and computed in binary64;
- *                FDLB_MIXED: populations stored, advected and relaxed in
- *                binary32; moment sums formed error-free in binary32 pairs
- *                and folded into binary64 per cell, so n, u, T (including
- *                the cancellation in T = (E - n u^2)/((D+K) n)), the
- *                Hermite factors and the relaxation coefficients are binary64
+ *                FDLB_MIXED: populations stored as binary32 pairs (high
+ *                part + residual); the MP-9 advection runs in binary32 on
+ *                the high part shifted by a per-tile reference, the stage
+ *                increments are kept as binary32 residuals relative to the
+ *                high part; per-cell moment sums are binary64, so n, u, T
+ *                (including the cancellation in T = (E - n u^2)/((D+K) n))
+ *                are binary64, and the equilibrium factors are binary32
+ *                pairs
  *   cuda_stream: cudaStream_t to enqueue on (NULL: the legacy default stream)
  *   out        : receives the context (NULL on failure)
  * The populations start at zero; call fdlb_init_riemann or fdlb_set_state. */
@@ -129,6 +135,12 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
  *   2-D: nq = 4, states = {rho, ux, uy, P} for quadrants 1 (x >= xsplit,
  *        y >= ysplit), 2 (x < xsplit, y >= ysplit), 3 (x < xsplit,
  *        y < ysplit) and 4 (x >= xsplit, y < ysplit).
+ * The side of a cell is decided in cell units: cell i lies right of (above)
+ * the membrane iff i + 1/2 >= s, s = (xsplit - x0) nx / (x1 - x0) computed in
+ * binary64 in that order (likewise in y).  s is exact for a membrane at the
+ * domain centre (s = nx/2), so with an odd cell count the middle cell, whose
+ * centre lies on the membrane, takes the right (upper) state.
+ * xsplit and ysplit must be finite (ysplit is ignored in 1-D).
  * states is a host array of nq*(d+2) doubles; rho > 0 and P > 0 required. */
 int fdlb_init_riemann(fdlb_ctx* ctx, const double* states, int nq, double xsplit, double ysplit);
 
@@ -166,7 +178,9 @@ int fdlb_moments_adjoint(fdlb_ctx* ctx, const double* nbar, const double* uxbar,
                          const double* uybar, const double* Tbar, double* Fbar);
 
 /* Copy the whole state F (layout above) out of / into the context.
- * fdlb_state_bytes gives the size: P * ncells * element size. */
+ * fdlb_state_bytes gives the size: P * ncells * 8 (binary64 in both
+ * precisions; FDLB_MIXED rounds each value to its binary32 pair on the way
+ * in and returns the pair's sum, correctly rounded, on the way out). */
 size_t fdlb_state_bytes(const fdlb_ctx* ctx);
 int fdlb_get_state(fdlb_ctx* ctx, void* dst, int on_device);
 int fdlb_set_state(fdlb_ctx* ctx, const void* src, int on_device);

@@ -493,15 +493,21 @@ int orc_advect(const orc_cfg* c, const double* F, double* LF) {
 /* 1-D: states[2][3] = (rho, u, P) left/right of xsplit.
  * 2-D: states[4][4] = (rho, ux, uy, P) of quadrants 1 (x>=xs, y>=ys),
  *      2 (x<xs, y>=ys), 3 (x<xs, y<ys), 4 (x>=xs, y<ys).
- * Cell centres x_s = x_left + (s - 1/2) ds; n = rho, T = P/rho (m = k_B = 1). */
+ * Cell centres x_s = x_left + (s - 1/2) ds; n = rho, T = P/rho (m = k_B = 1).
+ * A cell whose centre lies on a membrane takes the right (upper) state.  The
+ * test x_s >= xsplit is made in cell units, (s - 1/2) >= (xsplit - x_left)
+ * nx / (x_right - x_left): that quotient is exact for a membrane at the
+ * domain centre (nx/2), where rounded centres and a rounded ds would put the
+ * middle cell of some odd nx on the left. */
 int orc_init_states(const orc_cfg* c, const double* states, int nq, double xsplit,
                     double ysplit, double* F) {
   lattice L;
   if (make_lattice(c, &L)) return ORC_EINVAL;
   const int nx = c->nx, ny = (c->d == 2) ? c->ny : 1;
   const long N = (long)nx * ny;
-  const double dx = (c->x1 - c->x0) / nx;
-  const double dy = (c->d == 2) ? (c->y1 - c->y0) / ny : 0.0;
+  /* the membranes' positions in cells from the left (lower) edge */
+  const double mx = (xsplit - c->x0) * (double)nx / (c->x1 - c->x0);
+  const double my = (c->d == 2) ? (ysplit - c->y0) * (double)ny / (c->y1 - c->y0) : 0.0;
   if ((c->d == 1 && nq != 2) || (c->d == 2 && nq != 4)) return ORC_EINVAL;
   int bad = 0;
 #pragma omp parallel reduction(|| : bad)
@@ -510,16 +516,15 @@ int orc_init_states(const orc_cfg* c, const double* states, int nq, double xspli
 #pragma omp for schedule(static)
   for (int y = 0; y < ny; ++y) {
     for (int x = 0; x < nx; ++x) {
-      const double xc = c->x0 + (x + 0.5) * dx;
+      const int right = (x + 0.5 >= mx);
       double rho, u[2] = {0.0, 0.0}, P;
       if (c->d == 1) {
-        const double* s = states + 3 * ((xc >= xsplit) ? 1 : 0);
+        const double* s = states + 3 * right;
         rho = s[0]; u[0] = s[1]; P = s[2];
       } else {
-        const double yc = c->y0 + (y + 0.5) * dy;
         int quad;
-        if (yc >= ysplit) quad = (xc >= xsplit) ? 0 : 1;
-        else quad = (xc >= xsplit) ? 3 : 2;
+        if (y + 0.5 >= my) quad = right ? 0 : 1;
+        else quad = right ? 3 : 2;
         const double* s = states + 4 * quad;
         rho = s[0]; u[0] = s[1]; u[1] = s[2]; P = s[3];
       }

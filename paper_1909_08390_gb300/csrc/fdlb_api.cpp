@@ -276,24 +276,22 @@ int ensure_graph(fdlb_ctx* c) {
 }
 
 // Device buffers of a context: FDLB_FP64, six binary64 population arrays
-// (F, F2, F3, A4, A_fin, D); FDLB_MIXED, seven binary32 population arrays
-// (the two state buffers hi and lo, r3l, a4l, afl) and the per-cell mhi;
-// then the four moment fields for host copies, the status word, and the
-// FDLB_MIXED records (three of 2 recw binary32 components per cell).
+// (F, F2, F3, A4, A_fin, D); FDLB_MIXED, eleven binary32 population arrays
+// (the two state buffers hi and lo, r3l, a4l, afl, dm, fa, fb, fc) and the
+// per-cell mhi; then the four moment fields for host copies and the status
+// word.
 struct Layout {
-  size_t arr, mom, mhi, rec, total;
+  size_t arr, mom, mhi, total;
 };
 
-Layout buffer_layout(int precision, int P, int64_t N, int recw) {
+Layout buffer_layout(int precision, int P, int64_t N) {
   Layout L{};
   const size_t esize = precision == FDLB_MIXED ? sizeof(float) : sizeof(double);
   L.arr = ((size_t)P * (size_t)N * esize + 255) / 256 * 256;
-  const size_t narr = precision == FDLB_MIXED ? 7 : 6;
+  const size_t narr = precision == FDLB_MIXED ? 11 : 6;
   L.mom = narr * L.arr;
   L.mhi = L.mom + 4 * (size_t)N * sizeof(double) + 256;
-  L.rec = L.mhi + (precision == FDLB_MIXED ? 4 * (size_t)N * sizeof(double) : 0);
-  const size_t rec_one = (2 * (size_t)recw * (size_t)N * sizeof(float) + 255) / 256 * 256;
-  L.total = L.rec + 3 * rec_one;
+  L.total = L.mhi + (precision == FDLB_MIXED ? 4 * (size_t)N * sizeof(double) : 0);
   return L;
 }
 
@@ -307,6 +305,10 @@ void assign_buffers(fdlb_ctx* c, const Layout& L) {
     p.r3l = (float*)(b + 4 * L.arr);
     p.a4l = (float*)(b + 5 * L.arr);
     p.afl = (float*)(b + 6 * L.arr);
+    p.dm = (float*)(b + 7 * L.arr);
+    p.fa = (float*)(b + 8 * L.arr);
+    p.fb = (float*)(b + 9 * L.arr);
+    p.fc = (float*)(b + 10 * L.arr);
     p.mhi = (double*)(b + L.mhi);
     c->parity = 0;
     set_pair_pointers(c);
@@ -320,8 +322,6 @@ void assign_buffers(fdlb_ctx* c, const Layout& L) {
   }
   c->mom = (double*)(b + L.mom);
   p.status = (unsigned*)(b + L.mom + 4 * (size_t)p.N * sizeof(double));
-  const size_t rec_one = (2 * (size_t)p.recw * (size_t)p.N * sizeof(float) + 255) / 256 * 256;
-  for (int i = 0; i < 3; ++i) p.erec[i] = p.recw ? (float*)(b + L.rec + i * rec_one) : nullptr;
 }
 
 // A binary64 scratch array of P * N values for moving a FDLB_MIXED state to
@@ -569,9 +569,7 @@ int fdlb_create(const fdlb_grid* grid, int Qphi, int Qchi, double gamma, double 
     return cuda_err(nullptr, e, "cudaGetDevice");
   }
   p.precision = precision;
-  // binary32 contexts: three per-cell equilibrium records (fdlb_mixed.cu)
-  p.recw = precision == FDLB_MIXED ? fdlb::mixed_record_width(g.d, Qphi, Qchi) : 0;
-  const Layout lay = buffer_layout(precision, p.P, N, p.recw);
+  const Layout lay = buffer_layout(precision, p.P, N);
   c->buf_bytes = lay.total;
   e = cudaMalloc(&c->buf, c->buf_bytes);
   if (e != cudaSuccess) {
@@ -599,6 +597,8 @@ int fdlb_init_riemann(fdlb_ctx* c, const double* states, int nq, double xsplit, 
   if (!c) return set_err(nullptr, FDLB_EINVAL, "ctx is NULL");
   if (c->batch) return set_err(c, FDLB_EINVAL, "batch context: use fdlb_batch_init_riemann");
   if (!states) return set_err(c, FDLB_EINVAL, "states is NULL");
+  if (!std::isfinite(xsplit) || !std::isfinite(ysplit))
+    return set_err(c, FDLB_EINVAL, "non-finite membrane position");
   const int d = c->dp.d;
   if ((d == 1 && nq != 2) || (d == 2 && nq != 4))
     return set_err(c, FDLB_EINVAL, "nq must be 2 in 1-D and 4 in 2-D");
@@ -610,10 +610,9 @@ int fdlb_init_riemann(fdlb_ctx* c, const double* states, int nq, double xsplit, 
     if (!(rho > 0.0) || !(P > 0.0)) return set_err(c, FDLB_EINVAL, "rho and P must be > 0");
   }
   const fdlb_grid& g = c->grid;
-  const double dx = (g.x1 - g.x0) / (double)g.nx;
-  const double dy = (d == 2) ? (g.y1 - g.y0) / (double)g.ny : 0.0;
-  int e = fdlb::launch_init_riemann(c->dp, states, nq, xsplit, ysplit, g.x0, dx, g.y0, dy,
-                                    c->stream);
+  const double sx = fdlb::split_in_cells(xsplit, g.x0, g.x1, g.nx);
+  const double sy = (d == 2) ? fdlb::split_in_cells(ysplit, g.y0, g.y1, g.ny) : 0.0;
+  int e = fdlb::launch_init_riemann(c->dp, states, nq, sx, sy, c->stream);
   if (e) return cuda_err(c, (cudaError_t)e, "init kernel launch");
   c->prepared = false;
   return ensure_prepared(c);
@@ -851,8 +850,8 @@ int fdlb_create_batch(int nprob, const int64_t* nx, const double* gamma, double 
     b.invDK = 1.0 / DK;
     b.dtdx = dt / dx;
     b.x0 = x0;
-    b.dx = dx;
-    b.xsplit = 0.5 * (x0 + x1);
+    b.x1 = x1;
+    b.split = fdlb::split_in_cells(0.5 * (x0 + x1), x0, x1, nx[i]);
     total += nx[i];
     // the kernels index cells with 32-bit offsets
     if (total >= ((int64_t)1 << 31))
@@ -883,8 +882,7 @@ int fdlb_create_batch(int nprob, const int64_t* nx, const double* gamma, double 
   }
   p.bgrid = 4 * c->nsm;
   const size_t pstat_bytes = ((size_t)nprob * sizeof(unsigned) + 255) / 256 * 256;
-  p.recw = precision == FDLB_MIXED ? fdlb::mixed_record_width(1, Qphi, Qchi) : 0;
-  const Layout lay = buffer_layout(precision, p.P, total, p.recw);
+  const Layout lay = buffer_layout(precision, p.P, total);
   c->buf_bytes = lay.total + pstat_bytes;
   e = cudaMalloc(&c->buf, c->buf_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&c->probs_dev, nprob * sizeof(fdlb::BatchProblem));
@@ -925,7 +923,11 @@ int fdlb_batch_init_riemann(fdlb_ctx* c, const double* states, const double* xsp
         return set_err(c, FDLB_EINVAL, "problem %zu: rho and P must be finite and > 0", i);
       for (int j = 0; j < 3; ++j) c->probs[i].st[q][j] = st[j];
     }
-    if (xsplit) c->probs[i].xsplit = xsplit[i];
+    if (xsplit) {
+      if (!std::isfinite(xsplit[i])) return set_err(c, FDLB_EINVAL, "problem %zu: non-finite xsplit", i);
+      fdlb::BatchProblem& b = c->probs[i];
+      b.split = fdlb::split_in_cells(xsplit[i], b.x0, b.x1, b.nx);
+    }
   }
   int rc = upload_probs(c);
   if (rc) return rc;

@@ -360,6 +360,10 @@ __device__ __forceinline__ void cp_async_commit() {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
+// all but the most recently committed group complete
+__device__ __forceinline__ void cp_async_wait_1() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
 
 // Lattices of the batch kernels (1-D).
 #define FDLB_BATCH_LATTICES(X) \

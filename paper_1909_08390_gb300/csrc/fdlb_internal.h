@@ -37,10 +37,23 @@ struct BatchProblem {
   int pad_;
   double kchi, invDK;   // D+K-d and 1/(D+K) of this problem's gamma
   double dtdx;          // dt / dx
-  double x0, dx;        // domain start and cell size
-  double xsplit;        // membrane of the Riemann data
+  double x0, x1;        // domain
+  double split;         // membrane of the Riemann data in cell units (see
+                        // split_in_cells): cell i is right of it iff i + 1/2 >= split
   double st[2][3];      // (rho, u, P) left and right
 };
+
+// Position of a membrane in cell units, s = (split - lo) n / (hi - lo), each
+// operation rounded in binary64 in that order; cell i (centre lo + (i + 1/2)
+// (hi - lo)/n) takes the right or upper state iff i + 1/2 >= s.  s is exact
+// whenever the membrane sits on a cell face or centre of a grid whose length
+// is a power of two times a small integer, in particular at the domain
+// centre (s = n/2), so a cell centred there takes the right state as the
+// Riemann set-up of Sec. V reads; comparing rounded centres instead lets the
+// rounding of dx and of the centre move that cell to the left.
+inline double split_in_cells(double split, double lo, double hi, int64_t n) {
+  return ((split - lo) * (double)n) / (hi - lo);
+}
 
 // One tile of the batch work list: problem index and first cell.
 struct WorkItem {
@@ -86,17 +99,16 @@ struct DevParams {
   // FDLB_MIXED (fdlb_mixed.cu).  Each population of the state is an
   // unevaluated pair of binary32 values sh + sl (|sl| <= ulp(sh)/2), read
   // from (sh, sl) and written by the final stage to (nh, nl), the two buffers
-  // swapping roles every step.  The stage arrays hold the binary32 low parts
-  // of the explicit parts relative to the state's high part: R3 = sh + r3l,
-  // A4' = sh + a4l (then R4 = sh + a4l), A_fin = sh + afl.  mhi[4][N] holds
-  // per cell the binary64 moment sums (n, jx, jy, e) of sh.  erec[3] are
-  // per-cell records of the equilibrium factors of F^n, R3 and R4, each
-  // component a binary32 pair: recw high parts, then recw low parts, N apart.
+  // swapping roles every step.  The stage arrays hold binary32 low parts
+  // relative to the state's sh: R3 = sh + r3l, A4' = sh + a4l (then
+  // R4 = sh + a4l), A_fin = sh + afl; dm holds D = R - F_eq of the last
+  // stage; fa, fb, fc the low parts F2 - sh, F3 - sh, F4 - sh that stages 3,
+  // 4 and final advect.  mhi[4][N] holds per cell the binary64 moment sums
+  // (n, jx, jy, e) of sh.
   float *sh, *sl, *nh, *nl;
   float *r3l, *a4l, *afl;
+  float *dm, *fa, *fb, *fc;
   double* mhi;
-  float* erec[3];
-  int recw;
 };
 
 // 1-D tile shapes of the batch kernels, indexed by DevParams::variant:
@@ -109,8 +121,7 @@ enum Stage { kPrep = 0, kStage3 = 1, kStage4 = 2, kFinal = 3 };
 // Kernel launchers (fdlb_kernels.cu).  Each returns a cudaError_t value.
 bool supported_lattice(int d, int Qp, int Qc);
 int launch_stage(const DevParams& p, int stage, cudaStream_t s);
-int launch_init_riemann(const DevParams& p, const double* states, int nq, double xsplit,
-                        double ysplit, double x0, double dx, double y0, double dy,
+int launch_init_riemann(const DevParams& p, const double* states, int nq, double sx, double sy,
                         cudaStream_t s);
 int launch_moments(const DevParams& p, double* n, double* ux, double* uy, double* T,
                    cudaStream_t s);
@@ -120,10 +131,9 @@ int launch_moments_adjoint(const DevParams& p, const double* nbar, const double*
 // batch kernels (d = 1, several problems in one launch)
 int launch_batch_stage(const DevParams& p, int stage, cudaStream_t s);
 int launch_batch_init(const DevParams& p, cudaStream_t s);
-// binary32 single-pass stage kernels (fdlb_mixed.cu), single problems and
-// batches; mixed_setup raises the kernels' shared-memory limit (call once
-// before the first launch, outside stream capture)
-int mixed_record_width(int d, int Qp, int Qc);
+// binary32 stage kernels (fdlb_mixed.cu), single problems and batches;
+// mixed_setup raises the kernels' shared-memory limit (call once before the
+// first launch, outside stream capture)
 int mixed_setup(const DevParams& p);
 int launch_mixed_stage(const DevParams& p, int stage, cudaStream_t s);
 int launch_mixed_batch_stage(const DevParams& p, int stage, cudaStream_t s);

@@ -281,8 +281,7 @@ __global__ void batch_init_kernel(const __grid_constant__ DevParams p) {
   if (c >= p.N) return;
   const BatchProblem& bp = p.probs[find_problem(p, c)];
   const int x = (int)(c - bp.base);
-  const double xc = bp.x0 + (x + 0.5) * bp.dx;
-  const int q = (xc >= bp.xsplit) ? 1 : 0;
+  const int q = ((double)x + 0.5 >= bp.split) ? 1 : 0;
   const double rho = bp.st[q][0], ux = bp.st[q][1], P = bp.st[q][2];
   EqCell<1, QP, QC> eq64;
   make_eq_nut<1, QP, QC>(p, bp.kchi, rho, ux, 0.0, P / rho, eq64);
@@ -295,7 +294,7 @@ __global__ void batch_init_kernel(const __grid_constant__ DevParams p) {
 struct RiemannArgs {
   double st[4][4];
   int nq;
-  double xsplit, ysplit, x0, dx, y0, dy;
+  double sx, sy;  // membranes in cell units (split_in_cells)
 };
 
 template <int DIM, int QP, int QC, typename S>
@@ -305,13 +304,13 @@ __global__ void init_riemann_kernel(const __grid_constant__ DevParams p,
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.N) return;
   const int x = (int)(c % p.nx), y = (int)(c / p.nx);
-  const double xc = a.x0 + (x + 0.5) * a.dx;
+  const bool right = (double)x + 0.5 >= a.sx;
   int q;
   if (DIM == 1) {
-    q = (xc >= a.xsplit) ? 1 : 0;
+    q = right ? 1 : 0;
   } else {
-    const double yc = a.y0 + (y + 0.5) * a.dy;
-    q = (yc >= a.ysplit) ? ((xc >= a.xsplit) ? 0 : 1) : ((xc >= a.xsplit) ? 3 : 2);
+    const bool upper = (double)y + 0.5 >= a.sy;
+    q = upper ? (right ? 0 : 1) : (right ? 3 : 2);
   }
   const double rho = a.st[q][0];
   const double ux = a.st[q][1];
@@ -512,20 +511,15 @@ int launch_stage(const DevParams& p, int stage, cudaStream_t s) {
   return (int)cudaErrorInvalidValue;
 }
 
-int launch_init_riemann(const DevParams& p, const double* states, int nq, double xsplit,
-                        double ysplit, double x0, double dx, double y0, double dy,
+int launch_init_riemann(const DevParams& p, const double* states, int nq, double sx, double sy,
                         cudaStream_t s) {
   RiemannArgs a{};
   const int w = p.d + 2;
   for (int q = 0; q < nq && q < 4; ++q)
     for (int j = 0; j < w; ++j) a.st[q][j] = states[q * w + j];
   a.nq = nq;
-  a.xsplit = xsplit;
-  a.ysplit = ysplit;
-  a.x0 = x0;
-  a.dx = dx;
-  a.y0 = y0;
-  a.dy = dy;
+  a.sx = sx;
+  a.sy = sy;
 #define X(D_, P_, C_) \
   if (p.d == D_ && p.Qp == P_ && p.Qc == C_) return launch_init_t<D_, P_, C_>(p, a, s);
   FDLB_LATTICES(X)

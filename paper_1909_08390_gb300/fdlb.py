@@ -364,7 +364,7 @@ class Solver:
         self.P = fdlb_npop(self.ctx)
         self.N = fdlb_ncells(self.ctx)
         self.precision = precision
-        self.dtype = np.float64  # FDLB_MIXED states are exchanged as exact binary64 values
+        self.dtype = np.float64  # both precisions exchange the state as binary64
 
     @classmethod
     def from_workload(cls, wl, precision: int = FDLB_FP64, stream=None, **kw):
@@ -385,7 +385,7 @@ class Solver:
 
     def state(self) -> np.ndarray:
         """The populations as float64 (a FDLB_MIXED state's binary32 pairs
-        hi + lo are exact binary64 values)."""
+        hi + lo summed and rounded once)."""
         out = np.empty(self.shape, dtype=self.dtype)
         fdlb_get_state(self.ctx, out, False)
         return out
@@ -437,7 +437,7 @@ class BatchSolver(Solver):
         self.N = fdlb_ncells(self.ctx)
         self.nx = self.N
         self.precision = precision
-        self.dtype = np.float64  # FDLB_MIXED states are exchanged as exact binary64 values
+        self.dtype = np.float64  # both precisions exchange the state as binary64
         self.base = fdlb_batch_offsets(self.ctx, self.nprob)
 
     def init_riemann(self, states, xsplit=None):

@@ -19,8 +19,7 @@ bool supported_lattice(int d, int Qp, int Qc) {
   return (d == 1 || d == 2) && ((Qp == 8 && Qc == 8) || (Qp == 5 && Qc == 3) || (Qp == 3 && Qc == 3));
 }
 int launch_stage(const DevParams&, int, cudaStream_t) { return (int)cudaErrorNoDevice; }
-int launch_init_riemann(const DevParams&, const double*, int, double, double, double, double,
-                        double, double, cudaStream_t) {
+int launch_init_riemann(const DevParams&, const double*, int, double, double, cudaStream_t) {
   return (int)cudaErrorNoDevice;
 }
 int launch_moments(const DevParams&, double*, double*, double*, double*, cudaStream_t) {
@@ -33,7 +32,6 @@ int launch_moments_adjoint(const DevParams&, const double*, const double*, const
 int launch_batch_stage(const DevParams&, int, cudaStream_t) { return (int)cudaErrorNoDevice; }
 int launch_batch_init(const DevParams&, cudaStream_t) { return (int)cudaErrorNoDevice; }
 int batch_tile_cells(int) { return 127; }
-int mixed_record_width(int, int, int) { return 25; }
 int mixed_setup(const DevParams&) { return (int)cudaErrorNoDevice; }
 int launch_pair_to_double(const float*, const float*, double*, int64_t, cudaStream_t) {
   return (int)cudaErrorNoDevice;

@@ -110,6 +110,38 @@ def test_init_is_the_oracle_equilibrium(oracle, F):
             compare_state(pr, s.state(), want, tol=1e-14)
 
 
+def test_init_membrane_on_cell_centres(oracle, F):
+    """Membranes through cell centres (odd cell counts, membrane at the domain
+    centre) and on faces: every cell takes the same side as in the oracle, in
+    single problems (1-D and 2-D) and in a batch, within 1e-14.  nx = 49, 103
+    and 755 are lengths whose middle cell a rounded-centre comparison puts on
+    the left."""
+    st1 = [[0.884, -0.125, 0.164], [0.89, 0.267, 0.502]]
+    for nx in (3, 49, 103, 755, 400):
+        pr = problem(oracle, d=1, nx=nx, x0=-0.5, x1=0.5, Qphi=8, Qchi=8, gamma=1.2, tau=1e-6,
+                     dt=2e-5)
+        with solver(F, pr) as s:
+            s.init_riemann(st1, 0.0)
+            compare_state(pr, s.state(), oracle.init_states(pr, st1, 0.0), tol=1e-14)
+    pr = problem(oracle, d=2, nx=37, ny=29, x0=0.0, x1=1.0, y0=0.0, y1=1.0, Qphi=5, Qchi=3,
+                 gamma=1.4, tau=1e-5, dt=1e-4)
+    with solver(F, pr) as s:
+        s.init_riemann(W.C11_STATES, 0.5, 0.5)
+        compare_state(pr, s.state(), oracle.init_states(pr, W.C11_STATES, 0.5, 0.5), tol=1e-14)
+    nxs, gms = [49, 103, 755, 256, 107], [1.2, 1.4, 1.202, 1.6, 1.1]
+    st = np.array([st1] * len(nxs))
+    for prec in (0, 1):
+        with F.BatchSolver(nxs, gms, tau=1e-6, dt=2e-5, precision=prec) as b:
+            b.init_riemann(st)
+            got = b.state()
+        for j, (nx, g) in enumerate(zip(nxs, gms)):
+            pr = problem(oracle, d=1, nx=nx, x0=-0.5, x1=0.5, Qphi=8, Qchi=8, gamma=g, tau=1e-6,
+                         dt=2e-5)
+            want = oracle.init_states(pr, st1, 0.0)
+            # binary32 pairs hold about 48 bits of each population
+            compare_state(pr, b.member(got, j), want, tol=1e-14 if prec == 0 else 1e-13)
+
+
 @pytest.mark.parametrize("Q", [(8, 8), (5, 3), (3, 3)])
 @pytest.mark.parametrize("nx", [1, 4, 7, 128, 129, 333])
 @pytest.mark.parametrize("bc", [0, 1])

@@ -611,3 +611,57 @@ def test_periodic_ghosts_short_lines(oracle, S):
         b = oracle.advect_line(np.tile(F, rep), p, 0.1, bc=1)
         np.testing.assert_allclose(a, b[:S], rtol=0, atol=1e-14)
         np.testing.assert_allclose(a, b[S * (rep // 2):S * (rep // 2 + 1)], rtol=0, atol=1e-14)
+
+
+def _sides(oracle, pr, states, xs, ys=0.5):
+    """Which state each cell took: 1 where n is the second state's rho."""
+    n = oracle.moments(pr, oracle.init_states(pr, states, xs, ys))[0]
+    return n
+
+
+@pytest.mark.parametrize("nx", [1, 3, 49, 103, 107, 755, 4095])
+def test_membrane_on_a_cell_centre_takes_the_right_state(oracle, nx):
+    """Sec. V set-up with an odd cell count and the membrane at the domain
+    centre: the middle cell's centre lies exactly on it and it takes the right
+    state; every cell left of it the left state.  (Comparing rounded centres
+    x0 + (i + 1/2) dx with the membrane puts the middle cell on the left for
+    49, 103, 107 and 275 of the 2048 odd lengths up to 4096.)"""
+    pr = oracle.Problem(d=1, nx=nx, x0=-0.5, x1=0.5, Qphi=5, Qchi=3, gamma=1.4, tau=1e-5, dt=1e-5)
+    n = _sides(oracle, pr, [[1.0, 0.0, 1.0], [0.25, 0.0, 0.3]], 0.0)
+    mid = nx // 2
+    assert np.allclose(n[mid:], 0.25, rtol=1e-14) and np.allclose(n[:mid], 1.0, rtol=1e-14)
+
+
+def test_membrane_on_a_face_and_2d_centre(oracle):
+    """Even cell count: the membrane at the centre lies on a face, cells
+    nx/2 .. nx-1 are right of it.  2-D, 37 x 29 cells on [0, 1]^2 split at
+    (0.5, 0.5): the middle row and column (centres on the membranes) belong
+    to quadrant 1's side of each."""
+    pr = oracle.Problem(d=1, nx=40, x0=-0.5, x1=0.5, Qphi=5, Qchi=3, gamma=1.4, tau=1e-5, dt=1e-5)
+    n = _sides(oracle, pr, [[1.0, 0.0, 1.0], [0.25, 0.0, 0.3]], 0.0)
+    assert np.allclose(n[20:], 0.25) and np.allclose(n[:20], 1.0)
+    pr = oracle.Problem(d=2, nx=37, ny=29, x0=0.0, x1=1.0, y0=0.0, y1=1.0, Qphi=5, Qchi=3,
+                        gamma=1.4, tau=1e-5, dt=1e-5)
+    st = [[1.0, 0, 0, 1.0], [2.0, 0, 0, 1.0], [3.0, 0, 0, 1.0], [4.0, 0, 0, 1.0]]
+    n = _sides(oracle, pr, st, 0.5, 0.5)
+    want = np.empty((29, 37))
+    want[14:, 18:], want[14:, :18], want[:14, :18], want[:14, 18:] = 1.0, 2.0, 3.0, 4.0
+    assert np.allclose(n, want, rtol=1e-14)
+
+
+def test_membrane_side_is_the_exact_comparison(oracle):
+    """Seeded grids and membranes: a cell takes the right state exactly when
+    its centre x0 + (i + 1/2)(x1 - x0)/nx, evaluated in rational arithmetic
+    from the binary64 inputs, lies at or beyond the membrane."""
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(41)
+    for _ in range(40):
+        nx = int(rng.integers(1, 300))
+        x0 = float(rng.uniform(-2.0, 0.0))
+        x1 = x0 + float(rng.uniform(0.1, 3.0))
+        xs = float(rng.uniform(x0 - 0.1, x1 + 0.1))
+        pr = oracle.Problem(d=1, nx=nx, x0=x0, x1=x1, Qphi=3, Qchi=3, gamma=1.4, tau=1.0, dt=1e-9)
+        n = _sides(oracle, pr, [[1.0, 0.0, 1.0], [0.25, 0.0, 0.3]], xs)
+        want = [0.25 if Fr(x0) + (i + Fr(1, 2)) * (Fr(x1) - Fr(x0)) / nx >= Fr(xs) else 1.0
+                for i in range(nx)]
+        assert np.allclose(n, want, rtol=1e-14), (nx, x0, x1, xs)
