@@ -46,6 +46,12 @@
 namespace fdlb {
 namespace {
 
+// 16-byte asynchronous copy, L2 only (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
 // ---- binary32 pairs: x = hi + lo with about 48 significant bits ----------
 // The classical error-free arithmetic (Dekker, Knuth): TwoSum for additions,
 // the fused multiply-add for the exact product error; the intrinsics keep
@@ -327,8 +333,14 @@ struct MixSmem {
   static constexpr int SY = DIM == 2 ? C::TY + 2 * H : 1;
   // staged cells: tile + halo without the 2-D corner blocks (staged_pos)
   static constexpr int NSC = DIM == 2 ? C::TY * SXH + 2 * H * C::TX : SXH;
-  float rawh[C::G][NSC];               // sh of the staged cells, as loaded
-  float rawf[C::G][NSC];               // the advected low parts, as loaded
+  // 2-D grids whose rows hold a multiple of 4 cells land whole 16-byte
+  // chunks: the H rows above and below the tile (its columns), and the
+  // tile's rows from 8 columns left to 8 columns right of it (the 5-cell
+  // halos rounded out to chunks); other tiles land cell by cell
+  static constexpr int NCL = DIM == 2 && C::TX % 4 == 0 ? 2 * H * C::TX + C::TY * (C::TX + 16) : 0;
+  static constexpr int NRAW = NCL > NSC ? NCL : NSC;
+  float rawh[C::G][NRAW];              // sh of the staged cells, as loaded
+  float rawf[C::G][NRAW];              // the advected low parts, as loaded
   float tile[C::G][SY][SX];            // advected values - ref
   // 2-D: flux differences of the cells along x and y (mp9_march_delta_fp32);
   // 1-D: interface values along x.  Rows of TX + 1 (TY + 1) floats: the odd
@@ -366,21 +378,36 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   const int tid = threadIdx.x;
   const int64_t N = p.N;
 
-  // this thread's staged cells: tile offset and cell offset from geo.base
-  // (-1: none)
-  int soff[J], goff[J];
+  // chunked landing (16-byte copies) for 2-D grids whose rows, and so all
+  // chunk addresses, are 16-byte aligned; else cell by cell
+  constexpr bool kCh = M::NCL > 0;
+  const bool chunked = kCh && (geo.nx % 4) == 0 && (geo.base % 4) == 0;
+  // this thread's staged cells: tile offset and landing slot (-1: none);
+  // cell by cell, slot e holds staged cell e, and 1-D keeps its offset from
+  // geo.base (2-D grids landed cell by cell recompute it)
+  int soff[J], loff[J], goff1[DIM == 1 ? J : 1];
 #pragma unroll
   for (int j = 0; j < J; ++j) {
     const int e = tid + j * NT;
     int r, c;
     staged_pos(e, DIM, TX, TY, r, c);
     soff[j] = r * SX + c;
-    goff[j] = -1;
+    loff[j] = -1;
     if (e < NSC) {
-      const int gx = wrap_or_clamp(x0 - H + c, geo.nx, p.bc);
-      const int gy = DIM == 2 ? wrap_or_clamp(y0 - H + r, geo.ny, p.bc) : 0;
-      goff[j] = gy * geo.nx + gx;
+      loff[j] = e;
+      if constexpr (DIM == 1) goff1[j] = wrap_or_clamp(x0 - H + c, geo.nx, p.bc);
+      if (chunked) loff[j] = chunk_slot(r, c, TX, TY, x0, geo.nx, p.bc);
     }
+  }
+  // the thread's chunks q = tid, tid + NT (chunk_offset; -1: not copied)
+  constexpr int NCHK = M::NCL / 4;
+  static_assert(!kCh || NCHK <= 2 * NT, "two chunks per thread at most");
+  int go[2] = {-1, -1};
+  if constexpr (kCh) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      if (chunked && tid + i * NT < NCHK)
+        go[i] = chunk_offset(tid + i * NT, TX, TY, x0, y0, geo.nx, geo.ny, p.bc);
   }
   // own cells of this thread: tid + k NT (coalesced in both passes); a slot
   // past the tile's cells takes cell 0's indices (its lane computes on them
@@ -437,8 +464,9 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
 
   const int tg = tid / (NLINE * NSEG);  // the thread's population in a group (march)
   const int tline = (tid / NSEG) % NLINE;
-  // each thread copies, and later reads, only its own staged cells, so its
-  // own wait on the copies orders them
+  // landed cell by cell, each thread copies, and later reads, only its own
+  // staged cells, so its own wait on the copies orders them; chunks are read
+  // by other threads, so a barrier follows the wait
   float refv[G];
   auto prefetch = [&](int gfirst) {
 #pragma unroll
@@ -447,12 +475,30 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
       if (pop >= L::P) break;
       const float* __restrict__ srch = Sh + (int64_t)pop * N + geo.base;
       const float* __restrict__ srcf = fin + (int64_t)pop * N + geo.base;
+      if (kCh && chunked) {
 #pragma unroll
-      for (int j = 0; j < J; ++j)
-        if (goff[j] >= 0) {
-          cp_async(&sm.rawh[g][tid + j * NT], srch + goff[j]);
-          cp_async(&sm.rawf[g][tid + j * NT], srcf + goff[j]);
-        }
+        for (int i = 0; i < 2; ++i)
+          if (go[i] >= 0) {
+            cp_async16(&sm.rawh[g][4 * (tid + i * NT)], srch + go[i]);
+            cp_async16(&sm.rawf[g][4 * (tid + i * NT)], srcf + go[i]);
+          }
+      } else {
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+          if (loff[j] >= 0) {
+            int o;
+            if constexpr (DIM == 1) {
+              o = goff1[j];
+            } else {
+              int r, c;
+              staged_pos(tid + j * NT, DIM, TX, TY, r, c);
+              o = wrap_or_clamp(y0 - H + r, geo.ny, p.bc) * geo.nx +
+                  wrap_or_clamp(x0 - H + c, geo.nx, p.bc);
+            }
+            cp_async(&sm.rawh[g][loff[j]], srch + o);
+            cp_async(&sm.rawf[g][loff[j]], srcf + o);
+          }
+      }
       refv[g] = DIM == 2 ? Sh[(int64_t)pop * N + cref] : 0.0f;
     }
     cp_async_commit();
@@ -461,9 +507,32 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   // into sm.own (each thread copies and reads only its own cells' slots):
   // D of the stage's input and the low parts it updates (stage 3: sl;
   // stage 4: a4l, afl; final: afl, sh)
+  // A 2-D tile wholly inside a grid of 16-byte aligned rows copies them as
+  // 16-byte chunks of 4 cells, any thread any chunk (the barrier before
+  // pass 1 orders them).
+  const bool own16 = DIM == 2 && TX % 4 == 0 && (geo.nx % 4) == 0 && (geo.base % 4) == 0 &&
+                     x0 + TX <= geo.nx && y0 + TY <= geo.ny;
   auto prefetch_own = [&](int gfirst) {
     const float* const src[3] = {p.dm, STAGE == kStage3 ? p.sl : (STAGE == kStage4 ? p.a4l : p.afl),
                                  STAGE == kStage4 ? p.afl : Sh};
+    if constexpr (DIM == 2) {
+      if (own16 && gfirst + G <= L::P) {
+        constexpr int CH = CELLS / 4;  // chunks per population and array
+        constexpr int NCH = M::NOWN * G * CH;
+        static_assert(NCH % NT == 0, "whole chunks per thread");
+#pragma unroll
+        for (int i = 0; i < NCH / NT; ++i) {
+          const int q = tid + i * NT;
+          const int a = q / (G * CH), g = (q / CH) % G, cq = q % CH;
+          const int row = cq / (TX / 4), c4 = (cq % (TX / 4)) * 4;
+          const float* sa = a == 0 ? src[0] : (a == 1 ? src[1] : src[M::NOWN - 1]);
+          cp_async16(&sm.own[a][g][row * TX + c4],
+                     sa + (int64_t)(gfirst + g) * N + geo.base + (int64_t)(y0 + row) * geo.nx + x0 + c4);
+        }
+        cp_async_commit();
+        return;
+      }
+    }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int pop = gfirst + g;
@@ -486,8 +555,11 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   prefetch_own(0);
   for (int gi = 0; gi < NG; ++gi) {
     const int g0 = gi * G;  // first population of the group
-    // ---- stage the group: advected values - ref on tile + halo
+    // ---- stage the group: advected values - ref on tile + halo (chunks
+    // land from other threads: group 0's before this barrier, later groups'
+    // before the previous group's last barrier)
     cp_async_wait_1();
+    if (kCh && gi == 0) __syncthreads();
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int pop = g0 + g;
@@ -495,8 +567,8 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
       const float ref = refv[g];
 #pragma unroll
       for (int j = 0; j < J; ++j)
-        if (goff[j] >= 0) {
-          const int e = tid + j * NT;
+        if (loff[j] >= 0) {
+          const int e = loff[j];
           (&sm.tile[g][0][0])[soff[j]] = __fadd_rn(__fsub_rn(sm.rawh[g][e], ref), sm.rawf[g][e]);
         }
     }
@@ -622,6 +694,9 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
         }
       }
     }
+    // the next group's staged copies, the only ones in flight, complete
+    // before the barrier
+    if constexpr (kCh) cp_async_wait_all();
     __syncthreads();
     if (gi + 1 < NG) prefetch_own((gi + 1) * G);
   }

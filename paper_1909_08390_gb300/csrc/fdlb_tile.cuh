@@ -51,6 +51,45 @@ FDLB_HD void staged_pos(int e, int dim, int TX, int TY, int& r, int& c) {
   }
 }
 
+// Chunked landing of a 2-D tile (grids whose rows hold a multiple of 4
+// cells): the staged region is copied in 16-byte chunks of 4 cells into a
+// landing buffer of chunk_count(TX, TY) chunks, chunk q at slots 4q..4q+3:
+// first the kGhost rows above the tile (its TX columns, TX/4 chunks a row),
+// then the tile's TY rows from column x0 - 8 to x0 + TX + 8 ((TX+16)/4
+// chunks, the 5-cell halos rounded out to whole chunks), then the kGhost rows
+// below.  chunk_offset gives chunk q's first cell as an offset from the
+// population's first cell: rows clamp (outlet) or wrap (periodic) as a
+// whole; periodic columns wrap chunk by chunk; an outlet chunk reaching past
+// the left or right edge is not copied (-1), and chunk_slot sends the cells
+// that would read it to the edge column instead (the ghost value), which the
+// row's other chunks hold.  chunk_slot gives the landing slot of staged
+// position (r, c) (the tile's first cell at (kGhost, kGhost)).
+FDLB_HD int chunk_count(int TX, int TY) { return (2 * kGhost * TX + TY * (TX + 16)) / 4; }
+FDLB_HD int chunk_offset(int q, int TX, int TY, int x0, int y0, int nx, int ny, int bc) {
+  const int top = kGhost * TX / 4, mid = TY * (TX + 16) / 4;
+  int r, col;
+  if (q < top) {
+    r = q / (TX / 4);
+    col = x0 + (q % (TX / 4)) * 4;
+  } else if (q < top + mid) {
+    r = kGhost + (q - top) / ((TX + 16) / 4);
+    col = x0 - 8 + ((q - top) % ((TX + 16) / 4)) * 4;
+  } else {
+    r = kGhost + TY + (q - top - mid) / (TX / 4);
+    col = x0 + ((q - top - mid) % (TX / 4)) * 4;
+  }
+  const int rr = wrap_or_clamp(y0 - kGhost + r, ny, bc);
+  if (bc == 1) return rr * nx + wrap_or_clamp(col, nx, 1);
+  return (col >= 0 && col + 4 <= nx) ? rr * nx + col : -1;
+}
+FDLB_HD int chunk_slot(int r, int c, int TX, int TY, int x0, int nx, int bc) {
+  int cc = x0 - kGhost + c;
+  if (bc != 1) cc = cc < 0 ? 0 : (cc >= nx ? nx - 1 : cc);
+  if (r < kGhost) return r * TX + (cc - x0);
+  if (r < kGhost + TY) return kGhost * TX + (r - kGhost) * (TX + 16) + (cc - x0 + 8);
+  return kGhost * TX + TY * (TX + 16) + (r - kGhost - TY) * TX + (cc - x0);
+}
+
 // March task of thread tid for a group of populations: which population of
 // the group (tg), whether it marches an x line (in 2-D, lines 0..TY-1 are
 // the tile's rows, TY..TY+TX-1 its columns), and, for velocity sign sgn,

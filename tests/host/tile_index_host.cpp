@@ -2,6 +2,7 @@
 // for the CPU tests: every staged element, ghost source, own cell, march
 // read and interface write of every tile of a grid, checked to lie inside
 // its array, with staged positions and interface slots each covered once.
+// Also the chunked landing of 2-D tiles (16-byte copies of 4 cells).
 // Returns the number of violations (0 when all hold); prints the first few.
 #include <cstdio>
 #include <vector>
@@ -156,6 +157,43 @@ extern "C" int check_tiles(int dim, int TX, int TY, int SEG, int G, int NT, int 
       const int lx = c % TX, ly = c / TX;
       CHECK(lx + 1 <= TX && ly < TY && ly * TX + lx < CELLS, "own slot");
       if (dim == 2) CHECK(ly + 1 <= TY && lx < TX, "own y slot");
+    }
+  return bad;
+}
+
+// Chunked landing of a 2-D tile (chunk_offset, chunk_slot) on an nx x ny grid
+// with nx a multiple of 4: every tile, every copied chunk aligned and inside
+// the population, every chunk slot inside the landing buffer, and every
+// staged position reading a landed slot that holds the cell it needs (the
+// adjacent fluid node past an outlet edge, the periodic image otherwise).
+extern "C" int check_chunks(int TX, int TY, int nx, int ny, int bc) {
+  bad = 0;
+  const int H = kGhost;
+  const int NCHK = chunk_count(TX, TY);
+  const int NSC = staged_count(2, TX, TY);
+  CHECK(nx % 4 == 0 && TX % 4 == 0, "aligned rows");
+  for (int y0 = 0; y0 < ny; y0 += TY)
+    for (int x0 = 0; x0 < nx; x0 += TX) {
+      std::vector<long> land(4 * NCHK, -1);  // cell held by each slot
+      for (int q = 0; q < NCHK; ++q) {
+        const int o = chunk_offset(q, TX, TY, x0, y0, nx, ny, bc);
+        if (o < 0) {
+          CHECK(bc == 0, "periodic chunks are always copied");
+          continue;
+        }
+        CHECK(o % 4 == 0 && o + 3 < nx * ny, "chunk q=%d offset %d", q, o);
+        CHECK(o % nx + 3 < nx, "chunk within its row");
+        for (int k = 0; k < 4; ++k) land[4 * q + k] = o + k;
+      }
+      for (int e = 0; e < NSC; ++e) {
+        int r, c;
+        staged_pos(e, 2, TX, TY, r, c);
+        const int s = chunk_slot(r, c, TX, TY, x0, nx, bc);
+        CHECK(s >= 0 && s < 4 * NCHK, "slot e=%d s=%d", e, s);
+        if (!(s >= 0 && s < 4 * NCHK)) continue;
+        const long want = (long)wrap_or_clamp(y0 - H + r, ny, bc) * nx + wrap_or_clamp(x0 - H + c, nx, bc);
+        CHECK(land[s] == want, "tile (%d,%d) e=%d reads %ld, needs %ld", x0, y0, e, land[s], want);
+      }
     }
   return bad;
 }

@@ -30,6 +30,7 @@ def lib():
         os.replace(tmp, LIB)
     L = ctypes.CDLL(LIB)
     L.check_tiles.argtypes = [ctypes.c_int] * 9
+    L.check_chunks.argtypes = [ctypes.c_int] * 5
     return L
 
 
@@ -41,3 +42,13 @@ def test_tile_indices_stay_in_bounds(lib, shape, bc):
     for nx in sizes:
         for ny in (sizes if dim == 2 else [1]):
             assert lib.check_tiles(*shape, nx, ny, bc) == 0, (shape, nx, ny, bc)
+
+
+@pytest.mark.parametrize("bc", [0, 1])
+def test_chunked_landing_reads_the_right_cells(lib, bc):
+    """2-D tiles of grids whose rows hold a multiple of 4 cells land 16-byte
+    chunks; on grids narrower than a tile, ragged tiles and both boundaries,
+    each staged position reads the cell (or ghost source) it needs."""
+    for nx in (4, 8, 12, 16, 20, 36, 64):
+        for ny in (1, 5, 16, 17, 33):
+            assert lib.check_chunks(16, 16, nx, ny, bc) == 0, (nx, ny, bc)
