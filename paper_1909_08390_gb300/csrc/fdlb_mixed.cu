@@ -30,6 +30,12 @@
 // The relaxation is thus applied once per cell, by its owner, not on every
 // staged copy of the halo, and no equilibrium data reach memory.
 //
+// Copies.  On 2-D grids whose rows hold a multiple of 4 cells, the staged
+// tile and halo and the own cells' inputs arrive as 16-byte asynchronous
+// copies (chunks of 4 cells, fdlb_tile.cuh), and pass 2 of a tile inside
+// the grid streams its values through the then idle staging buffers, a ring
+// of four chunks copied three steps ahead; elsewhere copies are per cell.
+//
 // Moments: R3's and R4's are the binary64 per-cell sums of sh (mhi, left by
 // the previous final stage) plus binary32 sums of their low parts; the final
 // stage sums the new state's sh with error-free transformations (TwoSum and
@@ -41,6 +47,8 @@
 // (now R4's low part) and afl, then re-reads sh and a4l and writes D and fc;
 // the final stage stages sh and fc, reads D, afl and sh, writes the next
 // state nh, nl, then re-reads them and writes D and fa.
+#include <cstddef>
+
 #include "fdlb_device.cuh"
 
 namespace fdlb {
@@ -51,6 +59,19 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+
+template <int I>
+struct IC {
+  static constexpr int value = I;
+};
+template <int N, int I = 0, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(IC<I>{});
+    static_for<N, I + 1>(f);
+  }
+}
+__device__ __forceinline__ void cp_async_wait_2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 
 // ---- binary32 pairs: x = hi + lo with about 48 significant bits ----------
 // The classical error-free arithmetic (Dekker, Knuth): TwoSum for additions,
@@ -288,6 +309,96 @@ __device__ __forceinline__ void relax_cell(const DevParams& p, double kchi, doub
       cb[j] = nb[j];
     }
   }
+}
+
+// Pass 2 of a 2-D tile wholly inside a grid of 16-byte aligned rows: the
+// cells' values of R (a + b) stream through a ring of NB shared buffers, one
+// chunk (a row of the cell's equilibrium, for half of the tile's cells: the
+// cells tid, then tid + NT) per step, copied 16 bytes at a time three steps
+// ahead; each thread computes its own cell of every chunk, with the same
+// arithmetic as relax_cell.
+template <int DIM, int QP, int QC, int TX, int TY, int NT>
+__device__ __forceinline__ void relax_tile_streamed(const DevParams& p, double kchi, double invDK,
+                                                    int prob, const double (&mom)[2][4],
+                                                    int64_t N, int64_t cell0, int nx,
+                                                    const float* __restrict__ ain,
+                                                    const float* __restrict__ bin, float kd,
+                                                    float* __restrict__ fout, float* __restrict__ ring) {
+  using RW = EqRows<DIM, QP, QC>;
+  constexpr int HALF = NT;                 // cells of one chunk
+  constexpr int CS = 2 * kMaxRow * HALF;   // floats of one chunk buffer
+  constexpr int NB = 4;
+  constexpr int NS = 2 * RW::R;            // steps: two halves x rows
+  static_assert(TX * TY == 2 * NT && HALF % TX == 0, "two halves of whole rows");
+  const int tid = threadIdx.x;
+  // chunk s: half s / R, row s % R; slot (j, a, c) at (j * 2 + a) * HALF + c
+  auto issue = [&](int s) {
+    if (s < NS) {
+      const int k = s / RW::R, r = s % RW::R;
+      float* buf = ring + (s % NB) * CS;
+      constexpr int PER = 2 * kMaxRow * HALF / 4;  // 16-byte chunks
+#pragma unroll
+      for (int i = 0; i < (PER + NT - 1) / NT; ++i) {
+        const int q = tid + i * NT;
+        if (q < PER) {
+          const int ja = q / (HALF / 4), c4 = (q % (HALF / 4)) * 4;
+          const int j = ja >> 1, a = ja & 1;
+          if (j < RW::len(r)) {
+            const int ci = k * HALF + c4;  // tile cell of the chunk's first cell
+            const int64_t g = (int64_t)(RW::first(r) + j) * N + cell0 + (int64_t)(ci / TX) * nx + ci % TX;
+            cp_async16(buf + ja * HALF + c4, (a ? bin : ain) + g);
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+  issue(0);
+  issue(1);
+  issue(2);
+  EqFac<DIM, QP, QC> fac;
+  int64_t mycell = 0;
+#pragma unroll 1
+  for (int s = 0; s < NS; ++s) {
+    const int k = s / RW::R, r = s % RW::R;
+    if (r == 0) {
+      const double n = mom[k][0], jx = mom[k][1], jy = mom[k][2], e = mom[k][3];
+      const double inv_n = 1.0 / n;
+      const double ux = jx * inv_n;
+      const double uy = DIM == 2 ? jy * inv_n : 0.0;
+      const double T = (e - fma(jx, ux, jy * uy)) * inv_n * invDK;
+      const bool ok = n > 0.0 && T > 0.0 && isfinite(n) && isfinite(T) && isfinite(ux) && isfinite(uy);
+      if (!ok) {
+        atomicOr(p.status, 1u);
+        if (prob >= 0) atomicOr(&p.pstatus[prob], 1u);
+      }
+      eq_factors<DIM, QP, QC>(p, kchi, n, ux, uy, T, fac);
+      const int ci = k * HALF + tid;
+      mycell = cell0 + (int64_t)(ci / TX) * nx + ci % TX;
+    }
+    cp_async_wait_2();
+    __syncthreads();
+    const float* buf = ring + (s % NB) * CS;
+    // rows are unrolled through a switch so that factor indices stay static
+    auto row = [&](auto RR) {
+      constexpr int rr = decltype(RR)::value;
+      const DF rowf = eq_row_factor<DIM, QP, QC>(fac, rr);
+#pragma unroll
+      for (int j = 0; j < kMaxRow; ++j)
+        if (j < RW::len(rr)) {
+          const DF E = eq_in_row<DIM, QP, QC>(fac, rr, rowf, j);
+          const float a = buf[(2 * j) * HALF + tid], b = buf[(2 * j + 1) * HALF + tid];
+          const int64_t i = (int64_t)(RW::first(rr) + j) * N + mycell;
+          const float d = __fadd_rn(__fsub_rn(a, E.hi), __fsub_rn(b, E.lo));
+          p.dm[i] = d;
+          fout[i] = fmaf(-kd, d, b);
+        }
+    };
+    static_for<RW::R>([&](auto RR) { if (decltype(RR)::value == r) row(RR); });
+    issue(s + 3);
+  }
+  cp_async_wait_all();
+  __syncthreads();
 }
 
 // Plain binary32 moment sums of low parts, one cell or two (packed lanes).
@@ -714,6 +825,41 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   const float* __restrict__ const ain = STAGE == kFinal ? p.nh : Sh;
   const float* __restrict__ const bin = STAGE == kStage3 ? p.r3l : (STAGE == kStage4 ? p.a4l : p.nl);
   float* __restrict__ const fout = STAGE == kStage3 ? p.fb : (STAGE == kStage4 ? p.fc : p.fa);
+  if constexpr (DIM == 2 && CPT == 2 && TX * TY == 2 * NT) {
+    if (own16) {
+      double mm[2][4];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int64_t c = cell[k];
+        double mh[4];
+        if constexpr (STAGE == kFinal) {
+          const Moments m = to_fp64(mom[k]);
+          mh[0] = m.n;
+          mh[1] = m.jx;
+          mh[2] = m.jy;
+          mh[3] = m.e;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) p.mhi[i * N + c] = mh[i];
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) mh[i] = p.mhi[i * N + c];
+        }
+        mm[k][0] = mh[0] + (double)lm[k].n;
+        mm[k][1] = mh[1] + (double)lm[k].jx;
+        mm[k][2] = mh[2] + (double)lm[k].jy;
+        mm[k][3] = mh[3] + (double)lm[k].e;
+      }
+      // the ring takes the staging buffers, rawh (offset 0) up to coef,
+      // free once pass 1 has passed its last barrier
+      static_assert(sizeof(float) * 4 * 2 * kMaxRow * NT <= offsetof(M, coef),
+                    "the ring fits in the staging buffers");
+      relax_tile_streamed<DIM, QP, QC, TX, TY, NT>(p, geo.kchi, geo.invDK, geo.prob, mm, N,
+                                                   geo.base + (int64_t)y0 * geo.nx + x0, geo.nx,
+                                                   ain, bin, kd, fout, &sm.rawh[0][0]);
+      return;
+    }
+  }
+  // other tiles, cell by cell
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
     if (!valid[k]) continue;
