@@ -73,16 +73,16 @@ BYTES_PER_POP_MIXED = {k: 4 * n + MIXED_CELL_BYTES_PER_POP
 # ncu captures of the stage kernels on this workload, valid for the kernel sources
 # whose SHA-256 (over STAGE_KERNEL_SOURCES in that order, comments removed) is
 # recorded here; reported as null once that code differs.
-TRAFFIC_SRC_SHA256 = "0fab2c9867f14de4e0c541e78a5de548b751ae55b0b15be37306729500ac3fe7"
+TRAFFIC_SRC_SHA256 = "67639db8cf31480ae10e7a91ba450400e3e7fbcebfedeb027a1e27a9a98bf8d6"
 TRAFFIC_BYTES = {
-    "fp64": {"stage3": 2372572672, "stage4": 2354403584, "final": 1841189120},
-    "mixed": {"stage3": 553681664, "stage4": 693669888, "final": 440174848},
+    "fp64": {"stage3": 2371461120, "stage4": 2351332096, "final": 1847315968},
+    "mixed": {"stage3": 1522127360, "stage4": 1559397376, "final": 1380554496},
 }
 
 
 # The sources the stage kernels are compiled from.
 STAGE_KERNEL_SOURCES = ("fdlb_device.cuh", "fdlb_internal.h", "fdlb_kernels.cu", "fdlb_mixed.cu",
-                        "fdlb_mp9.cuh")
+                        "fdlb_mp9.cuh", "fdlb_tile.cuh")
 
 
 def _kernel_sources_sha256(root=None):
