@@ -507,6 +507,21 @@ def run_ours(args, world, rank, local):
                          "stage_ms_per_step": {n: v / args.steps for n, v in zip(names, mstage)}},
             "gpu_launches": launches_per_step * args.steps,
         }
+        # accuracy over a long run: both runs continued, untimed, to
+        # --long-steps steps from the same initial state
+        if args.long_steps > args.warmup + args.steps:
+            more = args.long_steps - args.warmup - args.steps
+            fdlb.fdlb_step(s.ctx, more)
+            fdlb.fdlb_step(m.ctx, more)
+            torch.cuda.synchronize()
+            (fn, fu, fv, fT), (mn, mu, mv, mT) = fields(s), fields(m)
+            l1err = lambda a, b, floor=0.0: float(np.abs(a - b).sum() / max(np.abs(b).sum(), floor * b.size))
+            mixed["err_vs_fp64_long"] = {
+                "after_steps": args.long_steps,
+                "max": {"n": relerr(mn, fn), "u": relerr(mu, fu, 1.0), "v": relerr(mv, fv, 1.0),
+                        "T": relerr(mT, fT)},
+                "l1": {"n": l1err(mn, fn), "u": l1err(mu, fu, 1.0), "v": l1err(mv, fv, 1.0),
+                       "T": l1err(mT, fT)}}
         m.close()
 
     # batched 1-D problems (512 two-state problems of uneven length and
@@ -725,6 +740,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--long-steps", type=int, default=2000,
+                    help="continue the binary64 and mixed runs (untimed) to this many steps and "
+                         "report their difference; 0: skip")
     ap.add_argument("--scale-n", type=int, default=2048)
     ap.add_argument("--scale-steps", type=int, default=0,
                     help="instead of the benchmark: the seeded quadrant problem at "
