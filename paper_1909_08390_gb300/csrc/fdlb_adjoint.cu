@@ -58,7 +58,7 @@ struct AdjParams {
   double* Fpart;       // direct part of the adjoint of F^n
   double* Dbar;        // adjoint of D
   double* Gnew;        // adjoint of F^n (output; may alias Gbar)
-  double* scal;        // kNumAdjScalars accumulators
+  double* scal;        // per block of the launch, kNumAdjScalars accumulators
 };
 
 // ---- frozen-limiter interface: value coefficients over the window ----------
@@ -333,11 +333,27 @@ __device__ __forceinline__ void advect_adjoint(const DevParams& p, const double*
   __syncthreads();
 }
 
-__device__ __forceinline__ void block_add(double* dst, double v) {
-  // warp sum then one atomic per warp
+// Adds the block's sums of v[i] to row[id[i]], this block's own row of
+// accumulators: a shuffle tree in each warp, then the warps' sums in warp
+// order.  No atomics, so the sums are the same on every run.  Every thread
+// of the block calls it (it holds a barrier); blockDim.x is a multiple of 32.
+template <int N>
+__device__ __forceinline__ void block_accumulate(double* __restrict__ row, const int (&id)[N],
+                                                 double (&v)[N]) {
+  __shared__ double ws[N][32];
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(dst, v);
+  for (int i = 0; i < N; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    if ((threadIdx.x & 31) == 0) ws[i][warp] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += ws[threadIdx.x][w];
+    row[id[threadIdx.x]] += t;
+  }
 }
 
 // ---- per-cell phases: 8 threads per cell ---------------------------------
@@ -521,9 +537,11 @@ __global__ void __launch_bounds__(kNT) adj4_kernel(const __grid_constant__ DevPa
     a.A4bar[pop * N + cell] = rb;
     a.X3bar[pop * N + cell] = -sc.wt3 * G[r] - sc.at43 * rb;
   }
-  block_add(&a.scal[kBarA44e4], s_a44);
-  block_add(&a.scal[kBarW4e4], s_w4);
-  block_add(&a.scal[kBarDK], s_dk);
+  {
+    const int id[3] = {kBarA44e4, kBarW4e4, kBarDK};
+    double v[3] = {s_a44, s_w4, s_dk};
+    block_accumulate<3>(a.scal + (int64_t)blockIdx.x * kNumAdjScalars, id, v);
+  }
 }
 
 // Stage 3.
@@ -601,13 +619,10 @@ __global__ void __launch_bounds__(kNT) adj3_kernel(const __grid_constant__ DevPa
     a.Dbar[pop * N + cell] = -sc.k3 * rb - sc.k4 * A4b[r] - sc.kf * G[r];
     a.X2bar[pop * N + cell] = -sc.at32 * rb - sc.at42 * A4b[r] - sc.wt2 * G[r];
   }
-  block_add(&a.scal[kBarA33e3], s[0]);
-  block_add(&a.scal[kBarA43e3], s[1]);
-  block_add(&a.scal[kBarW3e3], s[2]);
-  block_add(&a.scal[kBarK3], s[3]);
-  block_add(&a.scal[kBarK4], s[4]);
-  block_add(&a.scal[kBarKf], s[5]);
-  block_add(&a.scal[kBarDK], s[6]);
+  {
+    const int id[7] = {kBarA33e3, kBarA43e3, kBarW3e3, kBarK3, kBarK4, kBarKf, kBarDK};
+    block_accumulate<7>(a.scal + (int64_t)blockIdx.x * kNumAdjScalars, id, s);
+  }
 }
 
 // Stage 2 (and the stage-1/2 closed forms): adjoint of F^n.
@@ -663,8 +678,11 @@ __global__ void __launch_bounds__(kNT) adj2_kernel(const __grid_constant__ DevPa
     const double rb = pop < QP ? fma(p.p2[pop], ea.re, fma(p.px[pop], ea.rj, ea.rn)) : ea.re;
     a.Gnew[pop * N + cell] = a.Fpart[pop * N + cell] + Dt[r] + rb;
   }
-  block_add(&a.scal[kBarC2], s_c2);
-  block_add(&a.scal[kBarDK], s_dk);
+  {
+    const int id[2] = {kBarC2, kBarDK};
+    double v[2] = {s_c2, s_dk};
+    block_accumulate<2>(a.scal + (int64_t)blockIdx.x * kNumAdjScalars, id, v);
+  }
 }
 
 // ---- initial fields and their adjoint ---------------------------------------
@@ -727,7 +745,9 @@ __global__ void init_fields_adjoint_kernel(const __grid_constant__ DevParams p,
     ub[c] = su;
     Tb[c] = sT;
   }
-  block_add(dkbar, s_dk);
+  const int id[1] = {0};
+  double v[1] = {s_dk};
+  block_accumulate<1>(dkbar + blockIdx.x, id, v);
 }
 
 }  // namespace
@@ -815,24 +835,28 @@ int fdlb_init_fields_adjoint(fdlb_ctx* c, const double* Fbar, const double* n, c
     return fdlb::ctx_error(c, FDLB_EINVAL, "NULL argument");
   if (!adjoint_lattice(c))
     return fdlb::ctx_error(c, FDLB_EINVAL, "fdlb_init_fields_adjoint: 1-D binary64 outlet contexts");
-  double* dk = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&dk, sizeof(double), c->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(dk, 0, sizeof(double), c->stream);
-  if (e != cudaSuccess) return fdlb::ctx_error(c, FDLB_ECUDA, cudaGetErrorString(e));
+  // one D+K adjoint accumulator per block, summed here in block order
   const int nt = 128;
   const int64_t nb = (c->dp.N + nt - 1) / nt;
+  std::vector<double> hd((size_t)nb, 0.0);
+  double* dk = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&dk, (size_t)nb * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dk, 0, (size_t)nb * sizeof(double), c->stream);
+  if (e != cudaSuccess) return fdlb::ctx_error(c, FDLB_ECUDA, cudaGetErrorString(e));
   if (c->dp.Qp == 8)
     fdlb::init_fields_adjoint_kernel<8, 8><<<(unsigned)nb, nt, 0, c->stream>>>(c->dp, Fbar, n, u, T, nbar, ubar, Tbar, dk);
   else if (c->dp.Qp == 5)
     fdlb::init_fields_adjoint_kernel<5, 3><<<(unsigned)nb, nt, 0, c->stream>>>(c->dp, Fbar, n, u, T, nbar, ubar, Tbar, dk);
   else
     fdlb::init_fields_adjoint_kernel<3, 3><<<(unsigned)nb, nt, 0, c->stream>>>(c->dp, Fbar, n, u, T, nbar, ubar, Tbar, dk);
-  double h = 0.0;
   e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dk, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hd.data(), dk, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   cudaFreeAsync(dk, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return fdlb::ctx_error(c, FDLB_ECUDA, cudaGetErrorString(e));
+  double h = 0.0;
+  for (double x : hd) h += x;
   const double g = c->gamma;
   *dgamma = h * (-2.0 / ((g - 1.0) * (g - 1.0)));  // D + K = 2/(gamma - 1)
   return FDLB_OK;
@@ -880,7 +904,10 @@ int fdlb_adjoint(fdlb_ctx* c, int64_t nsteps, int every, const void* ckpt, doubl
   // saved F^n, F2, F3 and F4 (one more slot for the state after the
   // segment's last step); 5 adjoint arrays; the scalar accumulators
   const size_t seg_states = (size_t)(4 * every + 4);
-  const size_t need = (2 * seg_states + 5) * bytes + 256;
+  // the scalar accumulators: one row per block of the adjoint kernels
+  const int64_t nblk = (c->dp.nx + fdlb::kTX - 1) / fdlb::kTX;
+  const size_t scal_bytes = (size_t)nblk * fdlb::kNumAdjScalars * sizeof(double);
+  const size_t need = (2 * seg_states + 5) * bytes + scal_bytes + 256;
   if (c->adj_bytes < need) {
     if (c->adj_buf) cudaFree(c->adj_buf);
     c->adj_buf = nullptr;
@@ -915,7 +942,7 @@ int fdlb_adjoint(fdlb_ctx* c, int64_t nsteps, int every, const void* ckpt, doubl
     e = cudaEventCreateWithFlags(&rdone[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&adone[i], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, fdlb::kNumAdjScalars * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(scal, 0, scal_bytes, s);
   // the recompute stream starts after everything already queued on s
   if (e == cudaSuccess) e = cudaEventRecord(ev_start, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(rs, ev_start, 0);
@@ -988,10 +1015,14 @@ int fdlb_adjoint(fdlb_ctx* c, int64_t nsteps, int every, const void* ckpt, doubl
       cudaEventDestroy(tail);
     }
   }
-  double h[fdlb::kNumAdjScalars] = {0};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h, scal, sizeof h, cudaMemcpyDeviceToHost, s);
+  std::vector<double> rows((size_t)nblk * fdlb::kNumAdjScalars, 0.0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rows.data(), scal, scal_bytes, cudaMemcpyDeviceToHost, s);
   const cudaError_t es = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = es;
+  // the blocks' rows summed in block order
+  double h[fdlb::kNumAdjScalars] = {0};
+  for (int64_t b = 0; b < nblk; ++b)
+    for (int i = 0; i < fdlb::kNumAdjScalars; ++i) h[i] += rows[(size_t)b * fdlb::kNumAdjScalars + i];
   for (int i = 0; i < 2; ++i) {
     if (rdone[i]) cudaEventDestroy(rdone[i]);
     if (adone[i]) cudaEventDestroy(adone[i]);

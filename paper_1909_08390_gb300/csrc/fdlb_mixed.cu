@@ -60,17 +60,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
-template <int I>
-struct IC {
-  static constexpr int value = I;
-};
-template <int N, int I = 0, class F>
-__device__ __forceinline__ void static_for(F&& f) {
-  if constexpr (I < N) {
-    f(IC<I>{});
-    static_for<N, I + 1>(f);
-  }
-}
 __device__ __forceinline__ void cp_async_wait_2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 
 // ---- binary32 pairs: x = hi + lo with about 48 significant bits ----------
@@ -317,6 +306,16 @@ __device__ __forceinline__ void relax_cell(const DevParams& p, double kchi, doub
 // cells tid, then tid + NT) per step, copied 16 bytes at a time three steps
 // ahead; each thread computes its own cell of every chunk, with the same
 // arithmetic as relax_cell.
+// a[k] for a k known only at run time, by selects (no local memory)
+template <int Q>
+__device__ __forceinline__ DF pick_df(const DF (&a)[Q], int k) {
+  DF v = a[0];
+#pragma unroll
+  for (int i = 1; i < Q; ++i)
+    if (k == i) v = a[i];
+  return v;
+}
+
 template <int DIM, int QP, int QC, int TX, int TY, int NT>
 __device__ __forceinline__ void relax_tile_streamed(const DevParams& p, double kchi, double invDK,
                                                     int prob, const double (&mom)[2][4],
@@ -379,22 +378,28 @@ __device__ __forceinline__ void relax_tile_streamed(const DevParams& p, double k
     cp_async_wait_2();
     __syncthreads();
     const float* buf = ring + (s % NB) * CS;
-    // rows are unrolled through a switch so that factor indices stay static
-    auto row = [&](auto RR) {
-      constexpr int rr = decltype(RR)::value;
-      const DF rowf = eq_row_factor<DIM, QP, QC>(fac, rr);
+    // one copy of the row body: the row factor is picked at run time (the
+    // same factors and products as eq_row_factor, eq_in_row)
+    using FAC = EqFac<DIM, QP, QC>;
+    DF rowf;
+    if (r < QP) rowf = pick_df<QP>(fac.B, r);
+    else if constexpr (FAC::kSame) rowf = df_mul(fac.C, pick_df<QP>(fac.B, r - QP));
+    else rowf = pick_df<QC>(fac.Hy, r - QP);
+    const int len = RW::len(r), first = RW::first(r);
+    const bool phi_row = r < QP;
 #pragma unroll
-      for (int j = 0; j < kMaxRow; ++j)
-        if (j < RW::len(rr)) {
-          const DF E = eq_in_row<DIM, QP, QC>(fac, rr, rowf, j);
-          const float a = buf[(2 * j) * HALF + tid], b = buf[(2 * j + 1) * HALF + tid];
-          const int64_t i = (int64_t)(RW::first(rr) + j) * N + mycell;
-          const float d = __fadd_rn(__fsub_rn(a, E.hi), __fsub_rn(b, E.lo));
-          p.dm[i] = d;
-          fout[i] = fmaf(-kd, d, b);
-        }
-    };
-    static_for<RW::R>([&](auto RR) { if (decltype(RR)::value == r) row(RR); });
+    for (int j = 0; j < kMaxRow; ++j)
+      if (j < len) {
+        DF colf;
+        if constexpr (FAC::kSame) colf = fac.A[j < QP ? j : 0];
+        else colf = phi_row ? fac.A[j < QP ? j : 0] : fac.Hx[j < QC ? j : 0];
+        const DF E = pmul(colf, rowf);
+        const float a = buf[(2 * j) * HALF + tid], b = buf[(2 * j + 1) * HALF + tid];
+        const int64_t i = (int64_t)(first + j) * N + mycell;
+        const float d = __fadd_rn(__fsub_rn(a, E.hi), __fsub_rn(b, E.lo));
+        p.dm[i] = d;
+        fout[i] = fmaf(-kd, d, b);
+      }
     issue(s + 3);
   }
   cp_async_wait_all();
