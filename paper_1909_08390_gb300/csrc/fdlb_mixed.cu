@@ -470,7 +470,11 @@ struct MixSmem {
 
 // One tile of one stage.  Ends with every thread past its last use of the
 // shared memory, so a persistent CTA may start its next tile at once.
-template <int DIM, int QP, int QC, int STAGE, int VAR>
+// FAST: a 2-D grid whose sides are multiples of the tile's and whose
+// populations fill whole groups (every tile full, every row 16-byte
+// aligned), compiled without the per-cell copy and relaxation paths (the
+// kernels are sensitive to code size).
+template <int DIM, int QP, int QC, int STAGE, int VAR, bool FAST = false>
 __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, int x0, int y0,
                                            MixSmem<DIM, QP, QC, VAR, STAGE>& sm) {
   using C = TileCfg<DIM, VAR>;
@@ -497,7 +501,9 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   // chunked landing (16-byte copies) for 2-D grids whose rows, and so all
   // chunk addresses, are 16-byte aligned; else cell by cell
   constexpr bool kCh = M::NCL > 0;
-  const bool chunked = kCh && (geo.nx % 4) == 0 && (geo.base % 4) == 0;
+  constexpr bool kFast = FAST && DIM == 2 && kCh && L::P % G == 0;
+  static_assert(!FAST || kFast, "FAST needs 2-D chunked tiles and whole groups");
+  const bool chunked = kFast || (kCh && (geo.nx % 4) == 0 && (geo.base % 4) == 0);
   // this thread's staged cells: tile offset and landing slot (-1: none);
   // cell by cell, slot e holds staged cell e, and 1-D keeps its offset from
   // geo.base (2-D grids landed cell by cell recompute it)
@@ -591,14 +597,14 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
       if (pop >= L::P) break;
       const float* __restrict__ srch = Sh + (int64_t)pop * N + geo.base;
       const float* __restrict__ srcf = fin + (int64_t)pop * N + geo.base;
-      if (kCh && chunked) {
+      if (kFast || (kCh && chunked)) {
 #pragma unroll
         for (int i = 0; i < 2; ++i)
           if (go[i] >= 0) {
             cp_async16(&sm.rawh[g][4 * (tid + i * NT)], srch + go[i]);
             cp_async16(&sm.rawf[g][4 * (tid + i * NT)], srcf + go[i]);
           }
-      } else {
+      } else if constexpr (!kFast) {
 #pragma unroll
         for (int j = 0; j < J; ++j)
           if (loff[j] >= 0) {
@@ -626,13 +632,13 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   // A 2-D tile wholly inside a grid of 16-byte aligned rows copies them as
   // 16-byte chunks of 4 cells, any thread any chunk (the barrier before
   // pass 1 orders them).
-  const bool own16 = DIM == 2 && TX % 4 == 0 && (geo.nx % 4) == 0 && (geo.base % 4) == 0 &&
-                     x0 + TX <= geo.nx && y0 + TY <= geo.ny;
+  const bool own16 = kFast || (DIM == 2 && TX % 4 == 0 && (geo.nx % 4) == 0 && (geo.base % 4) == 0 &&
+                     x0 + TX <= geo.nx && y0 + TY <= geo.ny);
   auto prefetch_own = [&](int gfirst) {
     const float* const src[3] = {p.dm, STAGE == kStage3 ? p.sl : (STAGE == kStage4 ? p.a4l : p.afl),
                                  STAGE == kStage4 ? p.afl : Sh};
     if constexpr (DIM == 2) {
-      if (own16 && gfirst + G <= L::P) {
+      if (kFast || (own16 && gfirst + G <= L::P)) {
         constexpr int CH = CELLS / 4;  // chunks per population and array
         constexpr int NCH = M::NOWN * G * CH;
         static_assert(NCH % NT == 0, "whole chunks per thread");
@@ -831,7 +837,7 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   const float* __restrict__ const bin = STAGE == kStage3 ? p.r3l : (STAGE == kStage4 ? p.a4l : p.nl);
   float* __restrict__ const fout = STAGE == kStage3 ? p.fb : (STAGE == kStage4 ? p.fc : p.fa);
   if constexpr (DIM == 2 && CPT == 2 && TX * TY == 2 * NT) {
-    if (own16) {
+    if (kFast || own16) {
       double mm[2][4];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
@@ -888,15 +894,21 @@ __device__ __forceinline__ void mixed_tile(const DevParams& p, const Geo& geo, i
   }
 }
 
-template <int DIM, int QP, int QC, int STAGE, int VAR = 0>
+template <int DIM, int QP, int QC, int STAGE, int VAR = 0, bool FAST = false>
 __global__ void __launch_bounds__(TileCfg<DIM, VAR>::NT,
                                   DIM == 2 ? 4 : (TileCfg<DIM, VAR>::NT >= 128 ? 5 : 8))
     mixed_stage_kernel(const __grid_constant__ DevParams p) {
   extern __shared__ __align__(16) unsigned char smraw[];
   auto& sm = *reinterpret_cast<MixSmem<DIM, QP, QC, VAR, STAGE>*>(smraw);
   const Geo geo{p.nx, p.ny, 0, p.kchi, p.invDK, p.dtdx, p.dtdy, -1};
-  mixed_tile<DIM, QP, QC, STAGE, VAR>(p, geo, blockIdx.x * TileCfg<DIM, VAR>::TX,
-                                      blockIdx.y * TileCfg<DIM, VAR>::TY, sm);
+  mixed_tile<DIM, QP, QC, STAGE, VAR, FAST>(p, geo, blockIdx.x * TileCfg<DIM, VAR>::TX,
+                                            blockIdx.y * TileCfg<DIM, VAR>::TY, sm);
+}
+
+// whether a lattice has a FAST instance: 2-D, populations in whole groups
+template <int DIM, int QP, int QC>
+constexpr bool fast_lattice() {
+  return DIM == 2 && (QP * QP + QC * QC) % TileCfg<2, 0>::G == 0;
 }
 
 // (255-cell tiles carry two cells per thread: 3 CTAs per SM keep their
@@ -961,19 +973,19 @@ constexpr int smem_bytes() {
   return (int)sizeof(MixSmem<DIM, QP, QC, VAR, STAGE>);
 }
 
-template <int DIM, int QP, int QC, int VAR>
+template <int DIM, int QP, int QC, int VAR, bool FAST = false>
 int setup_tv() {
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage3, VAR>,
+    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage3, VAR, FAST>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              smem_bytes<DIM, QP, QC, VAR, kStage3>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage4, VAR>,
+    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kStage4, VAR, FAST>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              smem_bytes<DIM, QP, QC, VAR, kStage4>());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kFinal, VAR>,
+    e = cudaFuncSetAttribute(mixed_stage_kernel<DIM, QP, QC, kFinal, VAR, FAST>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                              smem_bytes<DIM, QP, QC, VAR, kFinal>());
   return (int)e;
@@ -982,6 +994,8 @@ int setup_tv() {
 template <int DIM, int QP, int QC>
 int setup_t() {
   int e = setup_tv<DIM, QP, QC, 0>();
+  if constexpr (fast_lattice<DIM, QP, QC>())
+    if (!e) e = setup_tv<DIM, QP, QC, 0, true>();
   if constexpr (DIM == 1) {
     if (!e) e = setup_tv<1, QP, QC, 1>();
     if (!e) e = setup_tv<1, QP, QC, 3>();
@@ -1008,21 +1022,21 @@ int setup_batch_v() {
   return (int)e;
 }
 
-template <int DIM, int QP, int QC, int VAR>
+template <int DIM, int QP, int QC, int VAR, bool FAST = false>
 int launch_tv(const DevParams& p, int stage, cudaStream_t s) {
   using C = TileCfg<DIM, VAR>;
   const dim3 grid((p.nx + C::TX - 1) / C::TX, DIM == 2 ? (p.ny + C::TY - 1) / C::TY : 1);
   switch (stage) {
     case kStage3:
-      mixed_stage_kernel<DIM, QP, QC, kStage3, VAR>
+      mixed_stage_kernel<DIM, QP, QC, kStage3, VAR, FAST>
           <<<grid, C::NT, smem_bytes<DIM, QP, QC, VAR, kStage3>(), s>>>(p);
       break;
     case kStage4:
-      mixed_stage_kernel<DIM, QP, QC, kStage4, VAR>
+      mixed_stage_kernel<DIM, QP, QC, kStage4, VAR, FAST>
           <<<grid, C::NT, smem_bytes<DIM, QP, QC, VAR, kStage4>(), s>>>(p);
       break;
     default:
-      mixed_stage_kernel<DIM, QP, QC, kFinal, VAR>
+      mixed_stage_kernel<DIM, QP, QC, kFinal, VAR, FAST>
           <<<grid, C::NT, smem_bytes<DIM, QP, QC, VAR, kFinal>(), s>>>(p);
       break;
   }
@@ -1048,6 +1062,11 @@ int launch_t(const DevParams& p, int stage, cudaStream_t s) {
       case 4: return launch_tv<1, QP, QC, 4>(p, stage, s);
       default: return launch_tv<1, QP, QC, 0>(p, stage, s);
     }
+  }
+  if constexpr (fast_lattice<DIM, QP, QC>()) {
+    // every tile full: the instance without the per-cell paths
+    if (p.nx % TileCfg<2, 0>::TX == 0 && p.ny % TileCfg<2, 0>::TY == 0)
+      return launch_tv<DIM, QP, QC, 0, true>(p, stage, s);
   }
   return launch_tv<DIM, QP, QC, 0>(p, stage, s);
 }
