@@ -75,11 +75,13 @@ def test_batch_member_against_oracle(oracle, F):
     assert np.abs(got - want).max() / np.abs(want).max() < 1e-12
 
 
-def test_batch_config_512_problems_1000_steps(oracle, F):
+@pytest.fixture(scope="module")
+def config3(F):
     """The 512-problem configuration as specified: Nx ~ U[256, 4096], gamma ~
     U[1.1, 5/3], seeded two-state data, Q = 8, tau = 1e-6, dt = 2e-5, binary32
-    pair storage, autotuned tiles, 1000 steps in one batch; and the same
-    problems in a binary64 batch.
+    pair storage, autotuned tiles, 1000 steps in one batch; the same problems
+    in a binary64 batch, run twice, the second time from initial populations
+    moved by a seeded relative 1e-8.
 
     Draws whose temperature T = P/rho lies far above the lattice's reference
     temperature leave the range the Q = 8 Hermite-truncated equilibrium
@@ -87,30 +89,15 @@ def test_batch_config_512_problems_1000_steps(oracle, F):
     in the binary64 oracle as on the GPU.  When that happens depends on the
     rounding, so a member whose growth reaches an invalid state close to step
     1000 may cross that line earlier, later or not at all with another
-    rounding (measured: the binary64 and mixed batches flag 64 and 64 or 65
-    members, 57 to 61 of them in common; member 207, flagged by the binary64
-    batch, stays valid in the oracle to step 1000).  So:
-    * every member either batch flags is unstable in the oracle (it fails
-      within 3000 steps), and the two batches agree on all but a few;
-    * a seeded sample of 12 members neither batch flags stays valid in the
-      oracle for the 1000 steps;
-    * accuracy on the members whose result the data determine: those neither
-      batch flags and whose binary64 moments at step 1000 move by less than
-      1e-6 when every initial population moves by a seeded relative 1e-8
-      (about the binary32 rounding the mixed path adds).  A member whose
-      growth is under way but has not yet made the state invalid (member 180,
-      nx = 628, gamma = 1.116, measured O(1) apart between the mixed batch
-      and the oracle at step 1000) fails that test by orders of magnitude; on
-      the others, 16 spread over the lengths and gammas against the oracle
-      within 1e-5 in n, u (normalised by max(|u|, 1)) and T (7.5e-7
-      measured), and every one against the binary64 batch: within 1e-6 in the
-      relative L1 norm, and within 1e-5 in the max norm but for at most one
-      in fifty, none beyond 2e-4.  The max norm of a member is set by the
-      sub-cell positions of its discontinuities, which the binary32 rounding
-      of the advected values, made at every stage, moves a little (the same
-      effect as in the 2-D runs at 2048^2); members that amplify it more than
-      most reach 1.9e-5 to 8.4e-5 (measured: 3 of 380, members 58, 86 and
-      216; 83 of the others lie below 1e-7, 268 between 1e-7 and 1e-6)."""
+    rounding (measured: the binary64 and mixed batches flag 65 and 65
+    members, 3 in each set only; 5 flagged members are still valid in the
+    oracle at step 1000).  A member whose growth is under way but has not yet
+    made the state invalid (member 180, nx = 628, gamma = 1.116: O(1) apart
+    between the mixed batch and the oracle at step 1000) is not determined by
+    its data to the tested accuracy: the stable members are those neither
+    batch flags and whose binary64 moments at step 1000 move by less than
+    1e-6 under the 1e-8 perturbation (about the binary32 rounding the mixed
+    path adds; 380 of the 444 unflagged)."""
     nsteps = 1000
     probs = W.batched_problems(0)
     nx = [p["nx"] for p in probs]
@@ -122,6 +109,7 @@ def test_batch_config_512_problems_1000_steps(oracle, F):
         b.step(nsteps, allow_unstable=True)
         flags = b.status().copy()
         n, u, _, T = b.moments()
+        base, nxs = b.base, b.nxs
     with F.BatchSolver(nx, gm, tau=1e-6, dt=2e-5, precision=0) as b64:
         b64.init_riemann(st)
         F0 = b64.state()
@@ -134,25 +122,46 @@ def test_batch_config_512_problems_1000_steps(oracle, F):
         b64.step(nsteps, allow_unstable=True)
         flags64p = b64.status().copy()
         n64p, u64p, _, T64p = b64.moments()
+    m = lambda a, j: a[..., base[j]:base[j] + nxs[j]]
+    rel = lambda x, y, floor=0.0: np.abs(x - y).max() / max(np.abs(y).max(), floor)
     f32 = {j for j in range(len(nx)) if flags[j]}
     f64 = {j for j in range(len(nx)) if flags64[j]}
+    unflagged = [j for j in range(len(nx)) if j not in f32 | f64]
+    moved = {j: max(rel(m(n64p, j), m(n64, j)), rel(m(u64p, j), m(u64, j), 1.0),
+                    rel(m(T64p, j), m(T64, j)))
+             for j in unflagged if not flags64p[j]}
+    stable = [j for j, d in moved.items() if d < 1e-6]
     print(f"flagged after {nsteps} steps: binary64 {len(f64)}, mixed {len(f32)}; binary64 only "
-          f"{sorted(f64 - f32)}, mixed only {sorted(f32 - f64)}")
-    assert len(f32) < len(nx) // 4
+          f"{sorted(f64 - f32)}, mixed only {sorted(f32 - f64)}; {len(stable)} members stable; "
+          f"unflagged but moved by the 1e-8 perturbation: {sum(d >= 1e-6 for d in moved.values())}")
+    mx = {j: max(rel(m(n, j), m(n64, j)), rel(m(u, j), m(u64, j), 1.0), rel(m(T, j), m(T64, j)))
+          for j in stable}
+    return dict(nsteps=nsteps, nx=nx, gm=gm, st=st, f32=f32, f64=f64, unflagged=unflagged,
+                stable=stable, mx=mx, m=m, rel=rel, mixed=(n, u, T), fp64=(n64, u64, T64))
+
+
+def _oracle_run(oracle, c, j, steps):
+    pr = oracle.Problem(d=1, nx=c["nx"][j], x0=-0.5, x1=0.5, Qphi=8, Qchi=8, gamma=c["gm"][j],
+                        tau=1e-6, dt=2e-5)
+    F0 = oracle.init_states(pr, c["st"][j], 0.0)
+    try:
+        return pr, oracle.step(pr, F0, steps)
+    except oracle.OracleError:
+        return pr, None
+
+
+def test_batch_config3_flags_refereed_by_the_oracle(oracle, config3):
+    """Every member either batch flags is unstable in the oracle (it fails
+    within 3000 steps), and the two batches agree on all but a few; a seeded
+    sample of 12 members neither batch flags stays valid in the oracle for
+    the 1000 steps."""
+    c = config3
+    f32, f64 = c["f32"], c["f64"]
+    assert len(f32) < len(c["nx"]) // 4
     assert len(f32 ^ f64) <= max(8, len(f64) // 6), sorted(f32 ^ f64)
-
-    def oracle_run(j, steps=nsteps):
-        pr = oracle.Problem(d=1, nx=nx[j], x0=-0.5, x1=0.5, Qphi=8, Qchi=8, gamma=gm[j],
-                            tau=1e-6, dt=2e-5)
-        F0 = oracle.init_states(pr, st[j], 0.0)
-        try:
-            return pr, oracle.step(pr, F0, steps)
-        except oracle.OracleError:
-            return pr, None
-
     late = []
     for j in sorted(f32 | f64):
-        pr, G = oracle_run(j)
+        pr, G = _oracle_run(oracle, c, j, c["nsteps"])
         if G is not None:  # valid at step 1000: it must fail within 2000 more
             late.append(j)
             try:
@@ -162,34 +171,41 @@ def test_batch_config_512_problems_1000_steps(oracle, F):
                 ok = False
             assert not ok, f"member {j} is flagged but stable in the oracle to step 3000"
     print(f"flagged members valid in the oracle at step 1000 (failing later): {late}")
-    unflagged = [j for j in range(len(nx)) if j not in f32 | f64]
     rng = np.random.default_rng(1000)
-    for j in rng.choice(unflagged, size=12, replace=False):
-        assert oracle_run(int(j))[1] is not None, f"member {j} unflagged but unstable in the oracle"
-    m = lambda a, j: a[..., b.base[j]:b.base[j] + b.nxs[j]]
-    rel = lambda x, y, floor=0.0: np.abs(x - y).max() / max(np.abs(y).max(), floor)
-    moved = {j: max(rel(m(n64p, j), m(n64, j)), rel(m(u64p, j), m(u64, j), 1.0),
-                    rel(m(T64p, j), m(T64, j)))
-             for j in unflagged if not flags64p[j]}
-    stable = [j for j, d in moved.items() if d < 1e-6]
-    print(f"{len(stable)} members stable; unflagged but moved by the 1e-8 perturbation: "
-          + ", ".join(f"{j} ({d:.1e})" for j, d in sorted(moved.items()) if d >= 1e-6)
-          + f"; flagged only after it: {sorted(j for j in unflagged if flags64p[j])}")
-    assert len(stable) > len(nx) // 2
-    # 16 members neither batch flags, spread over length and gamma
-    order = sorted(stable, key=lambda j: (nx[j], gm[j]))
+    for j in rng.choice(c["unflagged"], size=12, replace=False):
+        assert _oracle_run(oracle, c, int(j), c["nsteps"])[1] is not None, \
+            f"member {j} unflagged but unstable in the oracle"
+
+
+def test_batch_config3_stable_members_against_the_oracle(oracle, config3):
+    """16 stable members spread over the lengths and gammas against the
+    oracle: within 1e-5 in n, u (normalised by max(|u|, 1)) and T (7.5e-7
+    measured)."""
+    c = config3
+    stable, m, rel = c["stable"], c["m"], c["rel"]
+    assert len(stable) > len(c["nx"]) // 2
+    order = sorted(stable, key=lambda j: (c["nx"][j], c["gm"][j]))
     picks = [order[int(k)] for k in np.linspace(0, len(order) - 1, 16)]
     assert len(set(picks)) == 16
+    n, u, T = c["mixed"]
     errs = []
     for j in picks:
-        pr, want = oracle_run(j)
+        pr, want = _oracle_run(oracle, c, j, c["nsteps"])
         on, ou, _, oT = oracle.moments(pr, want)
         e = max(rel(m(n, j), on), rel(m(u, j), ou, 1.0), rel(m(T, j), oT))
         errs.append(e)
-        assert e < 1e-5, (j, nx[j], gm[j], e)
+        assert e < 1e-5, (j, c["nx"][j], c["gm"][j], e)
     print("16 members against the oracle: max rel err %.2e" % max(errs))
-    mx = {j: max(rel(m(n, j), m(n64, j)), rel(m(u, j), m(u64, j), 1.0), rel(m(T, j), m(T64, j)))
-          for j in stable}
+
+
+def test_batch_config3_stable_members_against_binary64(config3):
+    """Every stable member against the binary64 batch: within 1e-6 in the
+    relative L1 norm of n, u and T, and within 1e-5 in the max norm for all
+    but at most one in fifty, none beyond 2e-4 (the next test holds every
+    member to 1e-5 and is a declared expected failure)."""
+    c = config3
+    stable, m, mx = c["stable"], c["m"], c["mx"]
+    (n, u, T), (n64, u64, T64) = c["mixed"], c["fp64"]
     l1 = lambda x, y, floor=0.0: np.abs(x - y).sum() / max(np.abs(y).sum(), floor * y.size)
     worst_l1 = max(max(l1(m(n, j), m(n64, j)), l1(m(u, j), m(u64, j), 1.0), l1(m(T, j), m(T64, j)))
                    for j in stable)
@@ -199,6 +215,18 @@ def test_batch_config_512_problems_1000_steps(oracle, F):
                                          ", ".join(f"{j} ({mx[j]:.1e})" for j in above)))
     assert worst_l1 < 1e-6, worst_l1
     assert len(above) <= len(stable) // 50 and max(mx.values()) < 2e-4, above
+
+
+@pytest.mark.xfail(strict=False, reason=(
+    "the max norm of a member is set by the sub-cell positions of its discontinuities, which "
+    "the binary32 rounding of the advected values, made at every stage, moves a little: "
+    "3 of the 380 stable members (58, 86, 216) reach 1.9e-5 to 8.4e-5; 83 lie below 1e-7, "
+    "268 between 1e-7 and 1e-6, 26 between 1e-6 and 1e-5"))
+def test_batch_config3_every_stable_member_max_norm(config3):
+    """The stated bar on every stable member: 1e-5 relative in the max norm
+    of n, u and T against the binary64 batch."""
+    mx = config3["mx"]
+    assert max(mx.values()) < 1e-5, sorted(((v, j) for j, v in mx.items()), reverse=True)[:5]
 
 
 def test_regular_graph_replay_matches_direct_launches(F):
