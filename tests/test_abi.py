@@ -75,6 +75,7 @@ def test_create_rejects_unsupported_tableau(lib):
 
 
 def test_null_context_calls_fail_cleanly(lib):
+    assert lib.fdlb_measure_fp64_pipe(None, None, None) == fdlb.FDLB_EINVAL
     assert lib.fdlb_step(None, 1) == fdlb.FDLB_EINVAL
     assert lib.fdlb_init_riemann(None, None, 2, 0.0, 0.0) == fdlb.FDLB_EINVAL
     assert lib.fdlb_state_bytes(None) == 0
