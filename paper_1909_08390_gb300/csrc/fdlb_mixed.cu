@@ -35,6 +35,9 @@
 // copies (chunks of 4 cells, fdlb_tile.cuh), and pass 2 of a tile inside
 // the grid streams its values through the then idle staging buffers, a ring
 // of four chunks copied three steps ahead; elsewhere copies are per cell.
+// Grids whose sides are multiples of the 16-cell tile, on lattices whose
+// populations fill whole groups, run an instance compiled without the
+// per-cell paths (FAST): unexecuted code in these kernels costs time.
 //
 // Moments: R3's and R4's are the binary64 per-cell sums of sh (mhi, left by
 // the previous final stage) plus binary32 sums of their low parts; the final
