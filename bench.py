@@ -504,7 +504,12 @@ def run_ours(args, world, rank, local):
                          "frac": (m_gbs / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                          "traffic": _traffic("mixed", names[mt]), "avg_launch_ms": m_launch_ms,
-                         "stage_ms_per_step": {n: v / args.steps for n, v in zip(names, mstage)}},
+                         "stage_ms_per_step": {n: v / args.steps for n, v in zip(names, mstage)},
+                         # every stage kernel's fraction (the line's frac is the slowest's)
+                         "frac_by_stage": {
+                             n: (BYTES_PER_POP_MIXED[n] * units_per_step / (v / args.steps * 1e-3)
+                                 / 1e9 / peaks["hbm_gbs"]) if peaks.get("hbm_gbs") else None
+                             for n, v in zip(names, mstage)}},
             "gpu_launches": launches_per_step * args.steps,
         }
         # accuracy over a long run: both runs continued, untimed, to
