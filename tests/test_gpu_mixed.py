@@ -211,3 +211,35 @@ def test_mixed_512_long_run_against_fp64_gpu(F):
         mx = np.abs(a - b).max() / max(np.abs(b).max(), floor)
         print(f"512^2, 2000 steps, {name}: L1 {l1:.2e}, max {mx:.2e}")
         assert l1 < TOL and mx < TOL, (name, l1, mx)
+
+
+def test_config2_to_t025_mixed_against_fp64(F):
+    """The 512^2 seeded quadrant problem at its stated length, t = 0.25
+    (10 000 steps of dt = 2.5e-5), in both precisions: both stay valid
+    (n, T > 0 and finite), and the mixed run's n, u, v and T stay within 1e-5
+    of the binary64 run in the max norm and 1e-6 in L1 at steps 2000, 5000
+    and 10 000 (measured: max 3.3e-7, 4.7e-6, 6.2e-6; L1 6.3e-9, 3.6e-8,
+    6.2e-8)."""
+    wl = W.quadrant_2d(W.BENCH_SEED)
+    assert wl.nsteps == 10000 and abs(wl.nsteps * wl.dt - 0.25) < 1e-12
+    res = {}
+    for prec in (F.FDLB_FP64, F.FDLB_MIXED):
+        with F.Solver.from_workload(wl, precision=prec) as s:
+            s.init_riemann(wl.states, wl.xsplit, wl.ysplit)
+            done, out = 0, {}
+            for k in (2000, 5000, 10000):
+                s.step(k - done)  # raises on an invalid state
+                done = k
+                out[k] = s.moments()
+        res[prec] = out
+    rel = lambda a, b, floor=0.0: np.abs(a - b).max() / max(np.abs(b).max(), floor)
+    l1 = lambda a, b, floor=0.0: np.abs(a - b).sum() / max(np.abs(b).sum(), floor * b.size)
+    for k in (2000, 5000, 10000):
+        f, m = res[F.FDLB_FP64][k], res[F.FDLB_MIXED][k]
+        for fields in (f, m):
+            assert np.all(np.isfinite(fields[0])) and fields[0].min() > 0 and fields[3].min() > 0
+        mx = [rel(m[i], f[i], fl) for i, fl in ((0, 0.0), (1, 1.0), (2, 1.0), (3, 0.0))]
+        ls = [l1(m[i], f[i], fl) for i, fl in ((0, 0.0), (1, 1.0), (2, 1.0), (3, 0.0))]
+        print(f"512^2, {k} steps, mixed vs binary64: max {max(mx):.2e}, L1 {max(ls):.2e}")
+        assert max(mx) < 1e-5 and max(ls) < 1e-6, (k, mx, ls)
+
